@@ -1,0 +1,279 @@
+"""FP64 CPU oracle for the batched ORCA crowd step (test infrastructure).
+
+Only the tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  The product path (the CUDA library and
+its binding) never imports it, and the two share no code: the arithmetic here
+lives in ``orca_oracle.c`` (plain C, FP64, compiled with -ffp-contract=off),
+loaded with ctypes.
+
+Stages follow the per-step update of the paper's dynamic agents (Sec. 3.2,
+"Interactive Dynamics Generation") with the ORCA geometry of the method the
+paper cites for it (van den Berg et al., ISRR 2011):
+  O1 preferred velocity, O2 neighbours and nearby segments, O3 reciprocal agent
+  half-planes, O4 static-segment half-planes, O5 incremental 2D LP, O6
+  min-max-penetration fallback, O7 explicit Euler integration, O8 rollout
+  statistics (collision indicator and speed of the paper's metric table,
+  Appendix "Evaluation Metrics").
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "orca_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "liborca_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+ROBOT_STATUS = 2
+FALLBACK_STATUS = 1
+
+
+class Params(C.Structure):
+    _fields_ = [("tau", C.c_double), ("tau_obst", C.c_double), ("neighbor_dist", C.c_double),
+                ("dt", C.c_double), ("robot_alpha", C.c_double), ("max_neighbors", C.c_int32)]
+
+
+class Line(C.Structure):
+    _fields_ = [("qx", C.c_double), ("qy", C.c_double), ("nx", C.c_double), ("ny", C.c_double)]
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle library (gcc, FP64, no FMA contraction, OpenMP)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        tmp = _LIB_PATH + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fopenmp", "-fPIC",
+                               "-shared", "-std=c11", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            L = C.CDLL(build())
+            d, i32, i64, pd = C.c_double, C.c_int32, C.c_int64, C.POINTER(C.c_double)
+            pi32, pi64 = C.POINTER(C.c_int32), C.POINTER(C.c_int64)
+            L.or_pref_velocity.argtypes = [d, d, d, d, d, d, pd, pd]
+            L.or_rank_key.argtypes = [d, d, d, d]
+            L.or_rank_key.restype = d
+            L.or_neighbors.argtypes = [C.c_int, pd, C.c_int, d, C.c_int, pi32, pd]
+            L.or_neighbors.restype = C.c_int
+            L.or_seg_dist2.argtypes = [d, d, pd]
+            L.or_seg_dist2.restype = d
+            L.or_obstacles.argtypes = [C.c_int, pd, d, d, d, pi32]
+            L.or_obstacles.restype = C.c_int
+            L.or_agent_line.argtypes = [d] * 13 + [C.c_int, C.c_int, C.POINTER(Line)]
+            L.or_obstacle_line.argtypes = [d] * 6 + [pd, d, d, C.POINTER(Line)]
+            L.or_lp2.argtypes = [C.POINTER(Line), C.c_int, d, d, d, pd, pd]
+            L.or_lp2.restype = C.c_int
+            L.or_fallback.argtypes = [C.POINTER(Line), C.c_int, C.c_int, d, d, d, pd, pd, pd]
+            L.or_step.argtypes = [i32, pi64, pd, pd, pd, pi32, pi64, pd, C.POINTER(Params), pd, pd, pd, pd,
+                                  i64, pi64, pd, pd, pi32, pi32, C.c_int]
+            L.or_step.restype = C.c_int
+            L.or_collisions.argtypes = [i32, pi64, pd, pi64, pd, pd, pi64, pi64]
+            _lib = L
+    return _lib
+
+
+def _p(a, ct):
+    return a.ctypes.data_as(C.POINTER(ct))
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+# ------------------------------------------------------------------ single stages
+
+def pref_velocity(p, g, speed, dt):
+    """O1."""
+    vx, vy = C.c_double(), C.c_double()
+    lib().or_pref_velocity(float(p[0]), float(p[1]), float(g[0]), float(g[1]), float(speed), float(dt),
+                           C.byref(vx), C.byref(vy))
+    return np.array([vx.value, vy.value])
+
+
+def rank_key(pi, pj):
+    """O2 ranking key (FP64 squared distance, no FMA)."""
+    return lib().or_rank_key(float(pi[0]), float(pi[1]), float(pj[0]), float(pj[1]))
+
+
+def neighbors(pos, i, R, K):
+    """O2: env-local ids of the K nearest agents within R, ordered by (key, id)."""
+    pos = _f64(pos).reshape(-1, 2)
+    ids = np.zeros(max(K, 1), np.int32)
+    keys = np.zeros(max(K, 1), np.float64)
+    n = lib().or_neighbors(len(pos), _p(pos, C.c_double), int(i), float(R), int(K), _p(ids, C.c_int32),
+                           _p(keys, C.c_double))
+    return ids[:n].copy(), keys[:n].copy()
+
+
+def obstacles(segs, p, reach):
+    """O2 (segments): ids of segments closer than reach, ordered by (distance, id)."""
+    segs = _f64(segs).reshape(-1, 4)
+    ids = np.zeros(max(len(segs), 1), np.int32)
+    n = lib().or_obstacles(len(segs), _p(segs, C.c_double), float(p[0]), float(p[1]), float(reach),
+                           _p(ids, C.c_int32))
+    return ids[:n].copy()
+
+
+def agent_line(pi, vi, ri, pj, vj, rj, tau, dt, alpha=0.5, id_i=0, id_j=1):
+    """O3: returns (q, n) with the allowed side (v - q).n >= 0."""
+    ln = Line()
+    lib().or_agent_line(float(pi[0]), float(pi[1]), float(vi[0]), float(vi[1]), float(ri),
+                        float(pj[0]), float(pj[1]), float(vj[0]), float(vj[1]), float(rj),
+                        float(tau), float(dt), float(alpha), int(id_i), int(id_j), C.byref(ln))
+    return np.array([ln.qx, ln.qy]), np.array([ln.nx, ln.ny])
+
+
+def obstacle_line(p, v, r, vmax, seg, tau_o, dt):
+    """O4: returns (q, n)."""
+    ln = Line()
+    s = _f64(seg).reshape(4)
+    lib().or_obstacle_line(float(p[0]), float(p[1]), float(v[0]), float(v[1]), float(r), float(vmax),
+                           _p(s, C.c_double), float(tau_o), float(dt), C.byref(ln))
+    return np.array([ln.qx, ln.qy]), np.array([ln.nx, ln.ny])
+
+
+def _lines(lines):
+    arr = (Line * max(len(lines), 1))()
+    for k, (q, n) in enumerate(lines):
+        arr[k] = Line(float(q[0]), float(q[1]), float(n[0]), float(n[1]))
+    return arr
+
+
+def lp2(lines, vmax, pref):
+    """O5: returns (v, fail_index) with fail_index == len(lines) when feasible."""
+    arr = _lines(lines)
+    vx, vy = C.c_double(), C.c_double()
+    k = lib().or_lp2(arr, len(lines), float(vmax), float(pref[0]), float(pref[1]), C.byref(vx), C.byref(vy))
+    return np.array([vx.value, vy.value]), k
+
+
+def fallback(lines, n_hard, vmax, pref):
+    """O6: returns (v, d_star)."""
+    arr = _lines(lines)
+    vx, vy, ds = C.c_double(), C.c_double(), C.c_double()
+    lib().or_fallback(arr, len(lines), int(n_hard), float(vmax), float(pref[0]), float(pref[1]),
+                      C.byref(vx), C.byref(vy), C.byref(ds))
+    return np.array([vx.value, vy.value]), ds.value
+
+
+# ------------------------------------------------------------------ whole step
+
+def scene_params(scene):
+    return Params(scene.tau, scene.tau_obst, scene.neighbor_dist, scene.dt, scene.robot_responsibility,
+                  scene.max_neighbors)
+
+
+class OracleScene:
+    """FP64 copies of a Scene's static arrays, ready for repeated steps."""
+
+    def __init__(self, scene):
+        self.scene = scene
+        self.E = scene.n_envs
+        self.N = scene.n_agents
+        self.K = scene.max_neighbors
+        self.env_start = np.ascontiguousarray(scene.env_start, np.int64)
+        self.seg_start = np.ascontiguousarray(scene.seg_start, np.int64)
+        self.radius = _f64(scene.radius)
+        self.vmax = _f64(scene.max_speed)
+        self.pref = _f64(scene.pref_speed)
+        self.robot = np.ascontiguousarray(scene.robot_index, np.int32)
+        self.segs = _f64(scene.segments).reshape(-1, 4)
+        if self.segs.size == 0:
+            self.segs = np.zeros((1, 4))
+        self.goal = _f64(scene.goal)
+        self.params = scene_params(scene)
+        self.dt = scene.dt
+
+    def step(self, pos, vel, robot_vel=None, sel=None, threads=1, goal=None):
+        """O1-O7 for the selected agents (all when sel is None).
+
+        Returns (pos_out, vel_out, nbrs [N,K] env-local ids -1 padded, status [N]);
+        rows of unselected agents are left as NaN / -9."""
+        pos, vel = _f64(pos).reshape(-1, 2), _f64(vel).reshape(-1, 2)
+        goal = self.goal if goal is None else _f64(goal).reshape(-1, 2)
+        rv = _f64(np.zeros((self.E, 2)) if robot_vel is None else robot_vel).reshape(-1, 2)
+        po = np.full((self.N, 2), np.nan)
+        vo = np.full((self.N, 2), np.nan)
+        nb = np.full((self.N, max(self.K, 1)), -9, np.int32)
+        st = np.full(self.N, -9, np.int32)
+        if sel is None:
+            ns, sp = 0, None
+        else:
+            s = np.ascontiguousarray(sel, np.int64)
+            ns, sp = len(s), _p(s, C.c_int64)
+        rc = lib().or_step(self.E, _p(self.env_start, C.c_int64), _p(self.radius, C.c_double),
+                           _p(self.vmax, C.c_double), _p(self.pref, C.c_double), _p(self.robot, C.c_int32),
+                           _p(self.seg_start, C.c_int64), _p(self.segs, C.c_double), C.byref(self.params),
+                           _p(pos, C.c_double), _p(vel, C.c_double), _p(goal, C.c_double), _p(rv, C.c_double),
+                           ns, sp, _p(po, C.c_double), _p(vo, C.c_double), _p(nb, C.c_int32),
+                           _p(st, C.c_int32), int(threads))
+        if rc != 0:
+            raise ValueError("oracle step rejected its arguments")
+        return po, vo, nb[:, : self.K], st
+
+    def collisions(self, pos):
+        """O8: per-env (agent-pair, agent-segment) collision events of one state."""
+        pos = _f64(pos).reshape(-1, 2)
+        a = np.zeros(self.E, np.int64)
+        s = np.zeros(self.E, np.int64)
+        lib().or_collisions(self.E, _p(self.env_start, C.c_int64), _p(self.radius, C.c_double),
+                            _p(self.seg_start, C.c_int64), _p(self.segs, C.c_double), _p(pos, C.c_double),
+                            _p(a, C.c_int64), _p(s, C.c_int64))
+        return a, s
+
+
+def rollout(scene, steps, threads=1, record=False):
+    """Free-running FP64 rollout from the scene's initial state.
+
+    O8 statistics over the non-robot agents: collision events summed over the
+    post-integration states of every step (pairs involving the robot count),
+    mean speed over agents and steps, goal reach (first step with
+    |g - p| <= r), mean reach time in seconds and fraction reached.
+    """
+    o = OracleScene(scene)
+    pos = _f64(scene.pos).copy()
+    vel = _f64(scene.vel).copy()
+    ped = np.ones(o.N, bool)
+    for e in range(o.E):
+        if scene.robot_index[e] >= 0:
+            ped[o.env_start[e] + scene.robot_index[e]] = False
+    reach = np.full(o.N, -1, np.int64)
+    coll_a = coll_s = 0
+    speed_sum = 0.0
+    states = []
+    for k in range(steps):
+        pos, vel, _, _ = o.step(pos, vel, scene.robot_vel_at(k), threads=threads)
+        a, s = o.collisions(pos)
+        coll_a += int(a.sum())
+        coll_s += int(s.sum())
+        speed_sum += float(np.sqrt((vel[ped] ** 2).sum(1)).sum())
+        d = np.sqrt(((o.goal - pos) ** 2).sum(1))
+        newly = (reach < 0) & (d <= o.radius) & ped
+        reach[newly] = k + 1
+        if record:
+            states.append(np.concatenate([pos, vel], 1))
+    return _stats(reach, ped, coll_a, coll_s, speed_sum, steps, scene.dt, pos, vel, states if record else None)
+
+
+def _stats(reach, ped, coll_a, coll_s, speed_sum, steps, dt, pos, vel, states):
+    n_ped = int(ped.sum())
+    reached = (reach > 0) & ped
+    return dict(
+        collisions=coll_a + coll_s, agent_collisions=coll_a, segment_collisions=coll_s,
+        mean_speed=speed_sum / max(1, n_ped * steps),
+        reach_fraction=float(reached.sum()) / max(1, n_ped),
+        mean_reach_time=float(reach[reached].mean() * dt) if reached.any() else float("nan"),
+        reach_step=reach, final_pos=pos, final_vel=vel, states=states,
+    )
