@@ -1,0 +1,188 @@
+/*
+ * crowd.h -- C ABI of the batched ORCA crowd step on GB300 (sm_103a).
+ *
+ * The library moves the dynamic agents of many independent scene instances
+ * ("environments") one simulation step at a time: pedestrians avoid each
+ * other and the static segment obstacles of their block with ORCA, and each
+ * environment may hold one robot agent whose velocity is commanded from
+ * outside.  This is the per-step update of the paper's "Interactive Dynamics
+ * Generation" (Sec. 3.2): sample start and end points per agent, then adjust
+ * every agent in real time from proximity and relative velocity, across many
+ * parallel environments, reacting to the trained robot, all on the GPU.  The
+ * collision-avoidance rule is the ORCA method the paper cites (van den Berg
+ * et al., "Reciprocal n-body collision avoidance", ISRR 2011).
+ *
+ * One step, per agent, in order:
+ *   (A0) preferred velocity toward the goal; the robot takes its command;
+ *   (A1-A2) neighbours: agents of the same environment within the neighbour
+ *        distance R, ordered by (FP64 squared distance, index), first K;
+ *   (A3) one reciprocal half-plane per neighbour (truncated velocity obstacle,
+ *        horizon tau; horizon dt when already overlapping);
+ *   (A4) one half-plane per static segment within r + tau_obst * v_max;
+ *   (A5) the velocity closest to the preferred one inside the speed disk and
+ *        all half-planes; when none exists, the velocity of least maximal
+ *        penetration of the agent half-planes (segment half-planes stay hard),
+ *        ties broken by closeness to the preferred velocity;
+ *   (A6) explicit Euler: v <- v*, p <- p + dt v*; every agent moves from the
+ *        step-start state of its environment.
+ *
+ * Conventions
+ *   - SI units.  Agents are stored environment-major: environment e owns the
+ *     agents [sum_{f<e} agents_per_env[f], ... + agents_per_env[e]).
+ *     Segments likewise, with segs_per_env.
+ *   - Every buffer passed in is copied during the call; the caller keeps
+ *     ownership.  ptr_kind says whether a pointer is host (CROWD_HOST) or
+ *     device (CROWD_DEVICE) memory; device pointers must be on the handle's
+ *     device.
+ *   - All calls enqueue on the handle's CUDA stream and return before the GPU
+ *     finishes, except crowd_read_*, crowd_synchronize and crowd_destroy,
+ *     which wait for the stream.
+ *   - No exception crosses this interface: every call returns a crowd_status;
+ *     crowd_last_error() gives a message for the calling thread's last failure.
+ *   - A handle is not thread-safe: serialise calls on the same handle.
+ *   - Device-side faults of the algorithm (more than the supported number of
+ *     segment half-planes for one agent) set an error word that the next
+ *     synchronising call reports as CROWD_EDEVICE.
+ */
+#ifndef CROWD_H
+#define CROWD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct crowd_ctx* crowd_t;
+
+typedef enum {
+    CROWD_OK = 0,
+    CROWD_EINVAL = 1,  /* bad argument (NaN/Inf input, r <= 0, v_max < 0, K > 32, R <= 0, dt <= 0, ...) */
+    CROWD_ENOMEM = 2,  /* device allocation failed */
+    CROWD_ECUDA = 3,   /* a CUDA runtime call failed */
+    CROWD_EDEVICE = 4, /* the device error word was set by a kernel */
+    CROWD_ESTATE = 5   /* call out of order (e.g. a handle that failed earlier) */
+} crowd_status;
+
+enum { CROWD_HOST = 0, CROWD_DEVICE = 1 };
+
+/* crowd_params.flags */
+enum {
+    CROWD_FLAG_EXPORT_NEIGHBORS = 1, /* keep the neighbour lists of the last step (crowd_read_neighbors) */
+    CROWD_FLAG_STATS = 2,            /* accumulate rollout statistics (crowd_read_stats) */
+    CROWD_FLAG_COUNT_WORK = 4        /* count the algorithm's work items (crowd_read_work) */
+};
+
+/* Work counters (CROWD_FLAG_COUNT_WORK), summed over all agents and steps
+ * since the handle was created: the units the algorithmic operation count of
+ * one step is built from. */
+typedef struct {
+    uint64_t agent_steps;    /* agent updates performed */
+    uint64_t candidates;     /* neighbour candidates tested (agents of the 3x3 cell block) */
+    uint64_t agent_lines;    /* reciprocal agent half-planes built */
+    uint64_t obstacle_lines; /* static-segment half-planes built */
+    uint64_t segment_tests;  /* segment distance evaluations */
+    uint64_t lp_checks;      /* half-plane checks of the incremental LP */
+    uint64_t lp_solves;      /* 1D sub-solves (a line violated by the current point) */
+    uint64_t lp_solve_lines; /* previous lines scanned by those sub-solves */
+    uint64_t fallbacks;      /* agents whose LP was infeasible */
+} crowd_work;
+
+/* Maximum number of neighbours K. */
+#define CROWD_MAX_NEIGHBORS 32
+/* Maximum number of segment half-planes for one agent in one step. */
+#define CROWD_MAX_OBSTACLE_LINES 32
+
+typedef struct {
+    float time_horizon;         /* tau > 0, seconds (agents) */
+    float time_horizon_obst;    /* tau_obst >= 0, seconds (static segments); 0 means tau */
+    float neighbor_dist;        /* R > 0, metres */
+    int32_t max_neighbors;      /* K in [0, 32] */
+    float robot_responsibility; /* share of the avoidance an agent takes against the robot, in [0, 1]; ORCA's 1/2 */
+    int32_t flags;              /* CROWD_FLAG_* */
+} crowd_params;
+
+/* Per-environment rollout statistics (only with CROWD_FLAG_STATS), summed over
+ * the post-integration state of every step since the last reset:
+ *   agent_collisions: pairs i < j with |p_i - p_j| < r_i + r_j - 1e-6,
+ *   segment_collisions: (agent, segment) pairs closer than r_i - 1e-6,
+ *   speed_sum: sum of |v| over the non-robot agents,
+ *   steps: number of steps accumulated.
+ * These are the collision indicator and speed of the paper's metric table
+ * (Appendix, "Evaluation Metrics"). */
+typedef struct {
+    int64_t agent_collisions;
+    int64_t segment_collisions;
+    double speed_sum;
+    int64_t steps;
+} crowd_env_stats;
+
+/* Create a batch of n_envs environments on the current CUDA device.
+ *   agents_per_env [n_envs]     agents of each environment (>= 0)
+ *   radii, max_speeds [N]       r > 0, v_max >= 0 (N = total agents)
+ *   pref_speeds [N] or NULL     preferred walking speed; NULL means v_max
+ *   init_pos [N][2]             start positions; velocities start at 0
+ *   robot_index [n_envs] or NULL environment-local index of the robot agent, -1 for none
+ *   segs_per_env [n_envs] or NULL, segments [S][4] (ax, ay, bx, by) static segment obstacles; zero-length rejected
+ *   p                           parameters (copied)
+ *   cuda_stream                 cudaStream_t to enqueue on (NULL: the legacy default stream)
+ *   out                         receives the handle; owns all its device memory
+ * All pointers here are host pointers.  Goals start at the initial positions. */
+crowd_status crowd_create(int32_t n_envs, const int32_t* agents_per_env, const float* radii,
+                          const float* max_speeds, const float* pref_speeds, const float* init_pos,
+                          const int32_t* robot_index, const int32_t* segs_per_env, const float* segments,
+                          const crowd_params* p, void* cuda_stream, crowd_t* out);
+
+/* Goals [N][2]. */
+crowd_status crowd_set_goals(crowd_t h, const float* goals, int32_t ptr_kind);
+
+/* Full state [N][4] (px, py, vx, vy): resume from a checkpoint, or teacher
+ * forcing from another simulator's state. */
+crowd_status crowd_set_state(crowd_t h, const float* state, int32_t ptr_kind);
+
+/* Advance every environment by n_steps >= 1 steps of length dt > 0.
+ * robot_vel [n_steps][n_envs][2] m/s, the robot command of each step
+ * (entries of environments without a robot are ignored); NULL keeps every
+ * robot at its current velocity. */
+crowd_status crowd_step(crowd_t h, float dt, const float* robot_vel, int32_t ptr_kind, int32_t n_steps);
+
+/* Copy the state [N][4] (px, py, vx, vy) out; waits for the stream. */
+crowd_status crowd_read_state(crowd_t h, float* out, int32_t ptr_kind);
+
+/* Neighbour lists [N][K] of the last step (environment-local indices, -1
+ * padded), only with CROWD_FLAG_EXPORT_NEIGHBORS; waits for the stream. */
+crowd_status crowd_read_neighbors(crowd_t h, int32_t* out, int32_t ptr_kind);
+
+/* Host copies of the per-environment statistics [n_envs] and of the goal
+ * reach step of every agent [N] (1-based global step index after which
+ * |g - p| <= r first held, -1 if not yet); either may be NULL.  Waits. */
+crowd_status crowd_read_stats(crowd_t h, crowd_env_stats* env_stats, int32_t* reach_step);
+
+/* Host copy of the work counters (only with CROWD_FLAG_COUNT_WORK). */
+crowd_status crowd_read_work(crowd_t h, crowd_work* out);
+
+/* Zero the statistics and reach steps and restart the step counter at 0. */
+crowd_status crowd_reset_stats(crowd_t h);
+
+/* Wait for all work enqueued on the handle; reports a device error word. */
+crowd_status crowd_synchronize(crowd_t h);
+
+/* Release the handle and its device memory (waits for the stream first). */
+crowd_status crowd_destroy(crowd_t h);
+
+/* Number of agents / environments of a handle (0 for NULL). */
+int64_t crowd_num_agents(crowd_t h);
+int32_t crowd_num_envs(crowd_t h);
+
+/* Message for the calling thread's last failed call ("" if none). */
+const char* crowd_last_error(void);
+
+/* Library ABI version (increments on any signature change). */
+int32_t crowd_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CROWD_H */

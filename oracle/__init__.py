@@ -170,9 +170,14 @@ def fallback(lines, n_hard, vmax, pref):
 
 # ------------------------------------------------------------------ whole step
 
+def _f32(x):
+    return float(np.float32(x))
+
+
 def scene_params(scene):
-    return Params(scene.tau, scene.tau_obst, scene.neighbor_dist, scene.dt, scene.robot_responsibility,
-                  scene.max_neighbors)
+    """Scene parameters as the FP32 values the crowd library receives, held in FP64."""
+    return Params(_f32(scene.tau), _f32(scene.tau_obst), _f32(scene.neighbor_dist), _f32(scene.dt),
+                  _f32(scene.robot_responsibility), scene.max_neighbors)
 
 
 class OracleScene:
@@ -194,7 +199,7 @@ class OracleScene:
             self.segs = np.zeros((1, 4))
         self.goal = _f64(scene.goal)
         self.params = scene_params(scene)
-        self.dt = scene.dt
+        self.dt = self.params.dt
 
     def step(self, pos, vel, robot_vel=None, sel=None, threads=1, goal=None):
         """O1-O7 for the selected agents (all when sel is None).
@@ -264,7 +269,7 @@ def rollout(scene, steps, threads=1, record=False):
         reach[newly] = k + 1
         if record:
             states.append(np.concatenate([pos, vel], 1))
-    return _stats(reach, ped, coll_a, coll_s, speed_sum, steps, scene.dt, pos, vel, states if record else None)
+    return _stats(reach, ped, coll_a, coll_s, speed_sum, steps, o.dt, pos, vel, states if record else None)
 
 
 def _stats(reach, ped, coll_a, coll_s, speed_sum, steps, dt, pos, vel, states):

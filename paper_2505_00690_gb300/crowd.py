@@ -1,0 +1,264 @@
+"""Thin Python binding of the crowd C ABI (include/crowd.h).
+
+Argument marshalling only: every step of the crowd update runs in the CUDA
+library ``_build/libcrowd.so``.  The functions keep the C names; ``Crowd``
+wraps one handle.  Host arrays are numpy; device arrays are torch CUDA
+tensors (torch supplies device memory and streams, nothing else).  There is no
+CPU fallback: without the built library every call raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libcrowd.so")
+
+CROWD_OK, CROWD_EINVAL, CROWD_ENOMEM, CROWD_ECUDA, CROWD_EDEVICE, CROWD_ESTATE = range(6)
+CROWD_HOST, CROWD_DEVICE = 0, 1
+CROWD_FLAG_EXPORT_NEIGHBORS = 1
+CROWD_FLAG_STATS = 2
+CROWD_FLAG_COUNT_WORK = 4
+STATUS_NAMES = {0: "CROWD_OK", 1: "CROWD_EINVAL", 2: "CROWD_ENOMEM", 3: "CROWD_ECUDA", 4: "CROWD_EDEVICE",
+                5: "CROWD_ESTATE"}
+
+EXPORTED = ["crowd_create", "crowd_set_goals", "crowd_set_state", "crowd_step", "crowd_read_state",
+            "crowd_read_neighbors", "crowd_read_stats", "crowd_read_work", "crowd_reset_stats", "crowd_synchronize",
+            "crowd_destroy", "crowd_num_agents", "crowd_num_envs", "crowd_last_error", "crowd_abi_version"]
+
+
+class CrowdError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class crowd_params(C.Structure):
+    _fields_ = [("time_horizon", C.c_float), ("time_horizon_obst", C.c_float), ("neighbor_dist", C.c_float),
+                ("max_neighbors", C.c_int32), ("robot_responsibility", C.c_float), ("flags", C.c_int32)]
+
+
+class crowd_env_stats(C.Structure):
+    _fields_ = [("agent_collisions", C.c_int64), ("segment_collisions", C.c_int64), ("speed_sum", C.c_double),
+                ("steps", C.c_int64)]
+
+
+class crowd_work(C.Structure):
+    _fields_ = [(n, C.c_uint64) for n in ("agent_steps", "candidates", "agent_lines", "obstacle_lines",
+                                          "segment_tests", "lp_checks", "lp_solves", "lp_solve_lines",
+                                          "fallbacks")]
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libcrowd.so (raises if it was not built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"crowd CUDA library not built ({path}); run paper_2505_00690_gb300.build.build()")
+    L = C.CDLL(path)
+    vp, fp, ip, i32 = C.c_void_p, C.POINTER(C.c_float), C.POINTER(C.c_int32), C.c_int32
+    L.crowd_create.argtypes = [i32, vp, vp, vp, vp, vp, vp, vp, vp, C.POINTER(crowd_params), vp, C.POINTER(vp)]
+    L.crowd_set_goals.argtypes = [vp, vp, i32]
+    L.crowd_set_state.argtypes = [vp, vp, i32]
+    L.crowd_step.argtypes = [vp, C.c_float, vp, i32, i32]
+    L.crowd_read_state.argtypes = [vp, vp, i32]
+    L.crowd_read_neighbors.argtypes = [vp, vp, i32]
+    L.crowd_read_stats.argtypes = [vp, vp, vp]
+    L.crowd_read_work.argtypes = [vp, vp]
+    L.crowd_reset_stats.argtypes = [vp]
+    L.crowd_synchronize.argtypes = [vp]
+    L.crowd_destroy.argtypes = [vp]
+    L.crowd_num_agents.argtypes = [vp]
+    L.crowd_num_agents.restype = C.c_int64
+    L.crowd_num_envs.argtypes = [vp]
+    L.crowd_num_envs.restype = C.c_int32
+    L.crowd_last_error.restype = C.c_char_p
+    for name in EXPORTED:
+        if name not in ("crowd_num_agents", "crowd_num_envs", "crowd_last_error"):
+            getattr(L, name).restype = C.c_int
+    _lib = L
+    return L
+
+
+def _check(st):
+    if st != CROWD_OK:
+        raise CrowdError(st, (load().crowd_last_error() or b"").decode())
+
+
+def _host_ptr(a, dtype):
+    if a is None:
+        return None, None
+    arr = np.ascontiguousarray(a, dtype=dtype)
+    return arr, arr.ctypes.data_as(C.c_void_p)
+
+
+def _ptr(a, dtype):
+    """(keep-alive, pointer, ptr_kind) for a numpy array or a torch CUDA tensor."""
+    if a is None:
+        return None, None, CROWD_HOST
+    if hasattr(a, "is_cuda") and a.is_cuda:
+        import torch
+
+        want = {np.float32: torch.float32, np.int32: torch.int32}[dtype]
+        if a.dtype != want or not a.is_contiguous():
+            raise TypeError(f"device tensor must be contiguous {want}")
+        return a, C.c_void_p(a.data_ptr()), CROWD_DEVICE
+    arr, p = _host_ptr(a, dtype)
+    return arr, p, CROWD_HOST
+
+
+# ------------------------------------------------------------------ C names
+
+def crowd_create(n_envs, agents_per_env, radii, max_speeds, pref_speeds, init_pos, robot_index, segs_per_env,
+                 segments, params, cuda_stream=None):
+    L = load()
+    keep = []
+    ptrs = []
+    for a, dt in ((agents_per_env, np.int32), (radii, np.float32), (max_speeds, np.float32),
+                  (pref_speeds, np.float32), (init_pos, np.float32), (robot_index, np.int32),
+                  (segs_per_env, np.int32), (segments, np.float32)):
+        arr, p = _host_ptr(a, dt)
+        keep.append(arr)
+        ptrs.append(p)
+    h = C.c_void_p()
+    _check(L.crowd_create(int(n_envs), *ptrs, C.byref(params), C.c_void_p(cuda_stream or 0), C.byref(h)))
+    return h
+
+
+def crowd_set_goals(h, goals):
+    keep, p, kind = _ptr(goals, np.float32)
+    _check(load().crowd_set_goals(h, p, kind))
+
+
+def crowd_set_state(h, state):
+    keep, p, kind = _ptr(state, np.float32)
+    _check(load().crowd_set_state(h, p, kind))
+
+
+def crowd_step(h, dt, robot_vel=None, n_steps=1):
+    keep, p, kind = _ptr(robot_vel, np.float32)
+    _check(load().crowd_step(h, C.c_float(dt), p, kind, int(n_steps)))
+
+
+def crowd_read_state(h, out=None):
+    n = load().crowd_num_agents(h)
+    if out is None:
+        out = np.empty((n, 4), np.float32)
+    keep, p, kind = _ptr(out, np.float32)
+    if kind == CROWD_HOST and keep is not out:
+        raise TypeError("out must be a contiguous float32 array")
+    _check(load().crowd_read_state(h, p, kind))
+    return out
+
+
+def crowd_read_neighbors(h, K, out=None):
+    n = load().crowd_num_agents(h)
+    if out is None:
+        out = np.empty((n, K), np.int32)
+    keep, p, kind = _ptr(out, np.int32)
+    if kind == CROWD_HOST and keep is not out:
+        raise TypeError("out must be a contiguous int32 array")
+    _check(load().crowd_read_neighbors(h, p, kind))
+    return out
+
+
+def crowd_read_stats(h):
+    L = load()
+    E, N = L.crowd_num_envs(h), L.crowd_num_agents(h)
+    st = (crowd_env_stats * max(E, 1))()
+    reach = np.empty(max(N, 1), np.int32)
+    _check(L.crowd_read_stats(h, C.cast(st, C.c_void_p), reach.ctypes.data_as(C.c_void_p)))
+    env = [dict(agent_collisions=s.agent_collisions, segment_collisions=s.segment_collisions,
+                speed_sum=s.speed_sum, steps=s.steps) for s in st[:E]]
+    return env, reach[:N]
+
+
+def crowd_read_work(h):
+    w = crowd_work()
+    _check(load().crowd_read_work(h, C.byref(w)))
+    return {n: int(getattr(w, n)) for n, _ in crowd_work._fields_}
+
+
+def crowd_reset_stats(h):
+    _check(load().crowd_reset_stats(h))
+
+
+def crowd_synchronize(h):
+    _check(load().crowd_synchronize(h))
+
+
+def crowd_destroy(h):
+    _check(load().crowd_destroy(h))
+
+
+def crowd_last_error():
+    return (load().crowd_last_error() or b"").decode()
+
+
+# ------------------------------------------------------------------ convenience
+
+def params_for(scene, flags=0):
+    f = lambda x: float(np.float32(x))
+    return crowd_params(f(scene.tau), f(scene.tau_obst), f(scene.neighbor_dist), int(scene.max_neighbors),
+                        f(scene.robot_responsibility), int(flags))
+
+
+class Crowd:
+    """One crowd handle built from a Scene (see scenes.py)."""
+
+    def __init__(self, scene, flags=0, stream=None):
+        self.scene = scene
+        self.K = int(scene.max_neighbors)
+        self.N = scene.n_agents
+        self.E = scene.n_envs
+        self.params = params_for(scene, flags)
+        segs = scene.segments.reshape(-1, 4) if scene.segments.size else None
+        self.h = crowd_create(scene.n_envs, scene.agents_per_env, scene.radius, scene.max_speed, scene.pref_speed,
+                              scene.pos, scene.robot_index, scene.segs_per_env, segs, self.params, stream)
+        crowd_set_goals(self.h, scene.goal)
+        if np.any(scene.vel != 0):
+            crowd_set_state(self.h, scene.state())
+
+    def set_state(self, state):
+        crowd_set_state(self.h, state)
+
+    def set_goals(self, goals):
+        crowd_set_goals(self.h, goals)
+
+    def step(self, robot_vel=None, n_steps=1, dt=None):
+        crowd_step(self.h, self.scene.dt if dt is None else dt, robot_vel, n_steps)
+
+    def state(self, out=None):
+        return crowd_read_state(self.h, out)
+
+    def neighbors(self):
+        return crowd_read_neighbors(self.h, self.K)
+
+    def stats(self):
+        return crowd_read_stats(self.h)
+
+    def work(self):
+        return crowd_read_work(self.h)
+
+    def reset_stats(self):
+        crowd_reset_stats(self.h)
+
+    def synchronize(self):
+        crowd_synchronize(self.h)
+
+    def close(self):
+        if self.h is not None:
+            crowd_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

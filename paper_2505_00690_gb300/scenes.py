@@ -133,30 +133,48 @@ def _inside_any(px, py, polys):
 
 
 def _sample_points(rng, n, radii, lo, hi, segs, polys, separate=True, max_tries=200000):
-    """Draw n points in [lo, hi]^2 clear of obstacles and (optionally) of each other."""
+    """Draw n points in [lo, hi]^2 clear of obstacles and (optionally) of each other.
+
+    Candidates come in batches; obstacle clearance is tested for the whole
+    batch at once and mutual separation through a uniform hash of the points
+    already placed."""
+    radii = np.asarray(radii, np.float64)
     pts = np.zeros((n, 2), np.float64)
     placed = 0
     tries = 0
-    batch = 64
+    rmax = float(radii.max()) if n else 0.0
+    cell = 2.0 * rmax + CLEARANCE if rmax > 0 else 1.0
+    buckets = {}
+    batch = 256
     while placed < n:
         cand = rng.uniform(lo, hi, size=(batch, 2))
         tries += batch
         if tries > max_tries * max(1, n // 64 + 1):
             raise RuntimeError("spawn rejection sampling did not converge")
-        clear = _seg_point_dist(cand[:, 0], cand[:, 1], segs) >= radii[placed] + CLEARANCE if len(segs) else np.ones(batch, bool)
+        clear = np.ones(batch, bool)
+        if len(segs):
+            clear &= _seg_point_dist(cand[:, 0], cand[:, 1], segs) >= rmax + CLEARANCE
         if polys:
             clear &= ~_inside_any(cand[:, 0], cand[:, 1], polys)
-        for c, ok in zip(cand, clear):
+        for c in cand[clear]:
             if placed >= n:
                 break
-            if not ok:
-                continue
-            if len(segs) and _seg_point_dist(c[:1], c[1:], segs)[0] < radii[placed] + CLEARANCE:
-                continue
-            if separate and placed:
-                d = np.sqrt(((pts[:placed] - c) ** 2).sum(1))
-                if np.any(d < radii[:placed] + radii[placed] + CLEARANCE):
+            if separate:
+                cx, cy = int(math.floor(c[0] / cell)), int(math.floor(c[1] / cell))
+                ok = True
+                for gx in (cx - 1, cx, cx + 1):
+                    for gy in (cy - 1, cy, cy + 1):
+                        for k in buckets.get((gx, gy), ()):
+                            if math.hypot(pts[k, 0] - c[0], pts[k, 1] - c[1]) < radii[k] + radii[placed] + CLEARANCE:
+                                ok = False
+                                break
+                        if not ok:
+                            break
+                    if not ok:
+                        break
+                if not ok:
                     continue
+                buckets.setdefault((cx, cy), []).append(placed)
             pts[placed] = c
             placed += 1
     return pts

@@ -1,0 +1,274 @@
+"""GPU path vs the FP64 oracle, through the C ABI (needs a GB300).
+
+Contract (the crowd step of the paper's dynamic agents, Sec. 3.2):
+  - neighbour lists bit-exact: same ids in the same order (FP64 key, then id);
+  - per-step velocity within 1e-4 m/s under teacher forcing (both sides step
+    from the same FP32 state; the teacher is the oracle's own trajectory);
+  - positions within dt * 1e-4 plus FP32 rounding of the position;
+  - rollout statistics within 1 % (counts below 200 within +-2 events).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2505_00690_gb300 import scenes
+from paper_2505_00690_gb300.scenes import Scene
+
+pytestmark = pytest.mark.gpu
+
+VEL_TOL = 1e-4
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2505_00690_gb300 import build
+
+    build.build()
+
+
+def _crowd(scene, flags):
+    from paper_2505_00690_gb300 import crowd as cw
+
+    return cw.Crowd(scene, flags=flags)
+
+
+def _pos_tol(scene, pos):
+    return scene.dt * VEL_TOL + 4 * np.spacing(np.abs(pos).astype(np.float32)).astype(np.float64) + 1e-7
+
+
+def teacher_forced(scene, steps, sel=None):
+    """Step the GPU and the oracle from the same FP32 state for `steps` steps,
+    the next state being the oracle's.  Returns the worst velocity error, the
+    number of neighbour-list mismatches and the fallback count."""
+    from paper_2505_00690_gb300 import crowd as cw
+
+    cr = _crowd(scene, cw.CROWD_FLAG_EXPORT_NEIGHBORS)
+    o = oracle.OracleScene(scene)
+    S = scene.state().astype(np.float32)
+    worst, mism, fb = 0.0, 0, 0
+    for k in range(steps):
+        rv = scene.robot_vel_at(k).astype(np.float32)
+        cr.set_state(S)
+        cr.step(rv[None], n_steps=1)
+        G = cr.state()
+        nbG = cr.neighbors()
+        po, vo, nbO, st = o.step(S[:, :2], S[:, 2:], rv, sel=sel)
+        rows = np.arange(scene.n_agents) if sel is None else np.asarray(sel)
+        if scene.max_neighbors:
+            bad = np.any(nbG[rows] != nbO[rows], axis=1)
+            mism += int(bad.sum())
+            if bad.any():
+                r = rows[np.argmax(bad)]
+                print("neighbour mismatch at step", k, "agent", r, nbG[r], nbO[r])
+        err = np.abs(G[rows, 2:].astype(np.float64) - vo[rows]).max() if len(rows) else 0.0
+        perr = np.abs(G[rows, :2].astype(np.float64) - po[rows]) - _pos_tol(scene, po[rows])
+        assert perr.max(initial=-1) <= 0, (k, perr.max())
+        worst = max(worst, float(err))
+        fb += int((st[rows] == 1).sum())
+        if sel is None:
+            S = np.concatenate([po, vo], 1).astype(np.float32)
+        else:
+            S = G.copy()
+            S[rows] = np.concatenate([po[rows], vo[rows]], 1).astype(np.float32)
+    cr.close()
+    return worst, mism, fb
+
+
+def one_env(pos, vel, goal, radius, vmax, segs=(), robot=-1, R=5.0, K=10, tau=2.0, dt=0.1):
+    n = len(pos)
+    arr = lambda x: np.full(n, x, np.float32) if np.isscalar(x) else np.asarray(x, np.float32)
+    return Scene(name="edge", agents_per_env=np.array([n], np.int32), radius=arr(radius), max_speed=arr(vmax),
+                 pref_speed=arr(vmax), pos=np.asarray(pos, np.float32).reshape(-1, 2),
+                 vel=np.asarray(vel, np.float32).reshape(-1, 2), goal=np.asarray(goal, np.float32).reshape(-1, 2),
+                 robot_index=np.array([robot], np.int32), segs_per_env=np.array([len(segs)], np.int32),
+                 segments=np.asarray(segs, np.float32).reshape(-1, 4), tau=tau, tau_obst=tau, neighbor_dist=R,
+                 max_neighbors=K, dt=dt)
+
+
+# ----------------------------------------------------------------------------- teacher forcing
+
+def test_plain_square_teacher_forced():
+    sc = scenes.plain_square(0)
+    worst, mism, fb = teacher_forced(sc, 200)
+    assert mism == 0
+    assert worst <= VEL_TOL, worst
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_urban_block_subset_teacher_forced(seed):
+    sc = scenes.urban_block(seed, n_envs=6, steps=120)
+    worst, mism, fb = teacher_forced(sc, 120)
+    assert mism == 0
+    assert worst <= VEL_TOL, worst
+
+
+def test_uneven_polygons_teacher_forced():
+    sc = scenes.uneven_batch(3, n_envs=12, steps=60)
+    worst, mism, fb = teacher_forced(sc, 60)
+    assert mism == 0
+    assert worst <= VEL_TOL, worst
+
+
+def test_dense_cluster_with_fallbacks():
+    """A jammed ring walking to the opposite side: many infeasible LPs."""
+    n = 48
+    ang = np.linspace(0, 2 * np.pi, n, endpoint=False)
+    pos = np.stack([4 * np.cos(ang), 4 * np.sin(ang)], 1)
+    sc = one_env(pos, np.zeros((n, 2)), -pos, 0.3, 1.4, segs=[(-0.5, -0.5, 0.5, 0.5)])
+    worst, mism, fb = teacher_forced(sc, 80)
+    assert fb > 0
+    assert mism == 0
+    assert worst <= VEL_TOL, worst
+
+
+# ----------------------------------------------------------------------------- edge cases
+
+@pytest.mark.parametrize("sizes", [[1], [0, 5, 0], [31, 32, 33], [63, 64, 65, 1], [511, 512, 513]])
+def test_ragged_sizes(sizes):
+    rng = np.random.default_rng(sum(sizes))
+    envs = []
+    for n in sizes:
+        side = max(4.0, np.sqrt(max(n, 1) / 0.5))
+        envs.append(dict(radius=np.full(n, 0.2), max_speed=np.full(n, 1.2), pref_speed=np.full(n, 1.2),
+                         pos=scenes._sample_points(rng, n, np.full(n, 0.2), 0, side, [], []),
+                         vel=np.zeros((n, 2)), goal=rng.uniform(0, side, (n, 2)), segments=np.zeros((0, 4))))
+    sc = scenes._pack("ragged", envs)
+    worst, mism, fb = teacher_forced(sc, 20)
+    assert mism == 0 and worst <= VEL_TOL
+
+
+def test_largest_environment():
+    sc = scenes.uneven_batch(5, n_envs=1, n_lo=2048, n_hi=2048, max_polys=10, steps=5)
+    assert sc.n_agents == 2048
+    worst, mism, fb = teacher_forced(sc, 5)
+    assert mism == 0 and worst <= VEL_TOL
+
+
+def test_degenerate_geometry():
+    """Coincident agents, an agent exactly on a segment, K = 0 and K = 32."""
+    pos = [[0, 0], [0, 0], [3, 0], [3, 1e-7], [6, 1]]
+    vel = [[0.5, 0], [0, 0], [0, 0], [0, 0], [0, 0.5]]
+    goal = [[5, 5], [-5, -5], [3, 5], [3, -5], [6, 5]]
+    seg = [(5, 1, 7, 1)]  # agent 4 sits on it
+    for K in (0, 4, 32):
+        sc = one_env(pos, vel, goal, 0.3, 1.2, segs=seg, K=K)
+        worst, mism, fb = teacher_forced(sc, 10)
+        assert mism == 0 and worst <= VEL_TOL, (K, worst)
+
+
+def test_robot_agent_follows_command():
+    sc = scenes.urban_block(4, n_envs=3, n_peds=20, steps=10)
+    worst, mism, fb = teacher_forced(sc, 10)
+    assert mism == 0 and worst <= VEL_TOL
+
+
+# ----------------------------------------------------------------------------- full size, sampled
+
+def test_urban_block_full_size_sampled():
+    """All 256 urban blocks in one launch (the benchmark's configuration):
+    every 100 steps, one step is checked on 2000 sampled agents."""
+    from paper_2505_00690_gb300 import crowd as cw
+
+    sc = scenes.urban_block(0)
+    cr = _crowd(sc, cw.CROWD_FLAG_EXPORT_NEIGHBORS)
+    o = oracle.OracleScene(sc)
+    rng = np.random.default_rng(0)
+    k = 0
+    for chunk in [0, 100, 200, 300]:
+        if chunk > k:
+            cr.step(sc.robot_vel[k:chunk], n_steps=chunk - k)
+            k = chunk
+        S = cr.state()
+        rv = sc.robot_vel_at(k)
+        cr.step(rv[None], n_steps=1)
+        k += 1
+        G = cr.state()
+        nb = cr.neighbors()
+        sel = np.sort(rng.choice(sc.n_agents, 2000, replace=False))
+        po, vo, nbO, st = o.step(S[:, :2], S[:, 2:], rv, sel=sel)
+        assert np.array_equal(nb[sel], nbO[sel])
+        assert np.abs(G[sel, 2:] - vo[sel]).max() <= VEL_TOL
+    cr.close()
+
+
+# ----------------------------------------------------------------------------- batching / determinism
+
+def test_env_alone_equals_env_in_batch():
+    """Each environment's arithmetic is independent of the batch around it."""
+    from paper_2505_00690_gb300 import crowd as cw
+
+    sc = scenes.uneven_batch(7, n_envs=24, n_lo=16, n_hi=300, steps=30)
+    full = _crowd(sc, 0)
+    full.step(n_steps=30)
+    F = full.state()
+    es = sc.env_start
+    for e in [0, 5, 23]:
+        one = _crowd(sc.subset([e]), 0)
+        one.step(n_steps=30)
+        assert np.array_equal(one.state(), F[es[e]:es[e + 1]])
+        one.close()
+    full.close()
+
+
+def test_multi_step_call_equals_single_steps():
+    from paper_2505_00690_gb300 import crowd as cw
+
+    sc = scenes.urban_block(2, n_envs=4, steps=40)
+    a = _crowd(sc, 0)
+    a.step(sc.robot_vel[:40], n_steps=40)
+    b = _crowd(sc, 0)
+    for k in range(40):
+        b.step(sc.robot_vel[k:k + 1], n_steps=1)
+    assert np.array_equal(a.state(), b.state())
+
+
+def test_device_pointers_match_host_pointers():
+    import torch
+
+    sc = scenes.urban_block(3, n_envs=4, steps=20)
+    a = _crowd(sc, 0)
+    a.step(sc.robot_vel[:20], n_steps=20)
+    b = _crowd(sc, 0)
+    b.set_state(torch.from_numpy(sc.state()).cuda())
+    b.set_goals(torch.from_numpy(sc.goal).cuda())
+    b.step(torch.from_numpy(sc.robot_vel[:20]).cuda(), n_steps=20)
+    out = torch.empty((sc.n_agents, 4), dtype=torch.float32, device="cuda")
+    b.state(out)
+    assert np.array_equal(a.state(), out.cpu().numpy())
+
+
+# ----------------------------------------------------------------------------- rollout statistics
+
+def _close(a, b, rel=0.01, floor=0.0):
+    return abs(a - b) <= max(rel * max(abs(a), abs(b)), floor)
+
+
+@pytest.mark.parametrize("which", ["plain", "urban"])
+def test_rollout_statistics_within_one_percent(which):
+    from paper_2505_00690_gb300 import crowd as cw
+
+    sc = scenes.plain_square(0) if which == "plain" else scenes.urban_block(0, n_envs=16, steps=300)
+    steps = sc.steps
+    ref = oracle.rollout(sc, steps, threads=4)
+    cr = _crowd(sc, cw.CROWD_FLAG_STATS)
+    rv = sc.robot_vel[:steps] if sc.robot_vel is not None else None
+    cr.step(rv, n_steps=steps)
+    env, reach = cr.stats()
+    ped = np.ones(sc.n_agents, bool)
+    for e in range(sc.n_envs):
+        if sc.robot_index[e] >= 0:
+            ped[sc.env_start[e] + sc.robot_index[e]] = False
+    coll = sum(s["agent_collisions"] + s["segment_collisions"] for s in env)
+    mean_speed = sum(s["speed_sum"] for s in env) / (ped.sum() * steps)
+    reached = (reach > 0) & ped
+    frac = reached.sum() / ped.sum()
+    mrt = reach[reached].mean() * float(np.float32(sc.dt))
+    print(which, "gpu", coll, mean_speed, frac, mrt, "oracle", ref["collisions"], ref["mean_speed"],
+          ref["reach_fraction"], ref["mean_reach_time"])
+    assert _close(coll, ref["collisions"], floor=2 if max(coll, ref["collisions"]) < 200 else 0)
+    assert _close(mean_speed, ref["mean_speed"])
+    assert _close(mrt, ref["mean_reach_time"])
+    assert abs(frac - ref["reach_fraction"]) <= max(0.01, 1.0 / ped.sum())

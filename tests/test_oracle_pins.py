@@ -53,7 +53,7 @@ def test_lone_agent_closed_form():
     and stops exactly on it (p_k = p_0 + k dt s g_hat until arrival)."""
     p0 = np.array([1.0, 2.0])
     g = np.array([f32(7.0), f32(10.0)])  # 6-8-10 triangle: distance 10
-    s, dt = f32(1.25), 0.1
+    s, dt = f32(1.25), f32(0.1)
     sc = one_env([p0], [[0, 0]], [g], 0.3, s)
     o = oracle.OracleScene(sc)
     pos, vel = p0[None].copy(), np.zeros((1, 2))
@@ -94,7 +94,7 @@ def test_head_on_pair_closed_form(half_gap, steps):
     with its goals."""
     h = np.array(half_gap)
     e = h / np.linalg.norm(h)
-    r, s, tau, dt = f32(0.3), f32(1.4), 2.0, 0.1
+    r, s, tau, dt = f32(0.3), f32(1.4), 2.0, f32(0.1)
     pos = np.stack([-h, h])
     vel = np.stack([s * e, -s * e])
     goal = np.stack([100.0 * h, -100.0 * h])
@@ -136,7 +136,7 @@ def _in_vo_many(P, p, r, tau):
     return np.linalg.norm(t[..., None] * P - p, axis=-1) < r
 
 
-def _nearest_boundary(v, p, r, tau, ndir=1024, reach=12.0, step=2e-3):
+def _nearest_boundary(v, p, r, tau, ndir=512, reach=12.0, step=2e-3):
     """Brute force: shortest ray from v to a change of VO membership (a fine
     linear scan along each ray, so that thin parts of the VO are not stepped
     over, then bisection; the best direction is refined by golden section)."""
@@ -521,7 +521,8 @@ def test_neighbor_lists_are_the_k_smallest(seed):
 def _check_step_invariants(o, sc, pos, vel, robot_vel, nv, st):
     K = sc.max_neighbors
     es = sc.env_start
-    tau_o = sc.tau_obst
+    prm = o.params  # the FP32-rounded parameters the oracle steps with
+    tau_o, tau, dt, R, ra = prm.tau_obst, prm.tau, prm.dt, prm.neighbor_dist, prm.robot_alpha
     for e in range(sc.n_envs):
         base, n = es[e], es[e + 1] - es[e]
         segs = sc.segments[sc.seg_start[e]:sc.seg_start[e + 1]].astype(np.float64)
@@ -535,13 +536,13 @@ def _check_step_invariants(o, sc, pos, vel, robot_vel, nv, st):
                 continue
             vmax = float(sc.max_speed[g])
             assert np.linalg.norm(nv[g]) <= vmax * (1 + 1e-12) + 1e-15
-            ids, _ = oracle.neighbors(pos[base:base + n], i, sc.neighbor_dist, K)
+            ids, _ = oracle.neighbors(pos[base:base + n], i, R, K)
             oids = oracle.obstacles(segs, pos[g], float(sc.radius[g]) + tau_o * vmax) if len(segs) else []
-            lines = [oracle.obstacle_line(pos[g], V[i], sc.radius[g], vmax, segs[s], tau_o, sc.dt) for s in oids]
+            lines = [oracle.obstacle_line(pos[g], V[i], sc.radius[g], vmax, segs[s], tau_o, dt) for s in oids]
             for j in ids:
-                alpha = sc.robot_responsibility if j == robot else 0.5
+                alpha = ra if j == robot else 0.5
                 lines.append(oracle.agent_line(pos[g], V[i], sc.radius[g], pos[base + j], V[j],
-                                               sc.radius[base + j], sc.tau, sc.dt, alpha, i, j))
+                                               sc.radius[base + j], tau, dt, alpha, i, j))
             if st[g] == 0:
                 for q, nrm in lines:
                     assert (nv[g] - q) @ nrm >= -1e-9
@@ -562,7 +563,7 @@ def test_rollout_invariants(maker):
         rv = sc.robot_vel_at(k).astype(np.float64)
         npos, nvel, nb, st = o.step(pos, vel, rv)
         _check_step_invariants(o, sc, pos, vel, rv, nvel, st)
-        assert np.allclose(npos, pos + sc.dt * nvel, atol=1e-14)
+        assert np.allclose(npos, pos + o.params.dt * nvel, atol=1e-14)
         pos, vel = npos, nvel
 
 
