@@ -105,8 +105,9 @@ typedef struct {
 
 /* Per-environment rollout statistics (only with CROWD_FLAG_STATS), summed over
  * the post-integration state of every step since the last reset:
- *   agent_collisions: pairs i < j with |p_i - p_j| < r_i + r_j - 1e-6,
- *   segment_collisions: (agent, segment) pairs closer than r_i - 1e-6,
+ *   agent_collisions: pairs i < j with |p_i - p_j| < r_i + r_j - 0.001,
+ *   segment_collisions: (agent, segment) pairs closer than r_i - 0.001
+ *     (a collision is a penetration deeper than 1 mm),
  *   speed_sum: sum of |v| over the non-robot agents,
  *   steps: number of steps accumulated.
  * These are the collision indicator and speed of the paper's metric table

@@ -43,6 +43,7 @@
 #define OR_EPS_GOAL 1e-6 /* O1: distance under which the agent has arrived */
 #define OR_EPS_PAR 1e-9  /* O5: |det| at or below which two lines are parallel */
 #define OR_MAX_K 32
+#define OR_COLLIDE_DEPTH 1e-3 /* O8: penetration counted as a collision, metres */
 
 typedef struct {
     double tau;         /* time horizon for agents */
@@ -470,8 +471,10 @@ int or_step(int32_t n_envs, const int64_t* env_start, const double* radius, cons
 
 /* ---------------------------------------------------------------- O8 ---- */
 /* Collision events of one post-integration state, per env: pairs i < j with
- * |p_i - p_j| < r_i + r_j - 1e-6 and agent-segment pairs with distance
- * < r_i - 1e-6 (the collision indicator of the paper's metric table). */
+ * |p_i - p_j| < r_i + r_j - OR_COLLIDE_DEPTH and agent-segment pairs with
+ * distance < r_i - OR_COLLIDE_DEPTH (the collision indicator of the paper's
+ * metric table, counted from a penetration depth of 1 mm so that agents left
+ * exactly touching by ORCA are not counted on rounding noise). */
 void or_collisions(int32_t n_envs, const int64_t* env_start, const double* radius,
                    const int64_t* seg_start, const double* segs, const double* pos,
                    int64_t* agent_pairs_out, int64_t* seg_pairs_out)
@@ -481,12 +484,12 @@ void or_collisions(int32_t n_envs, const int64_t* env_start, const double* radiu
         for (int64_t i = env_start[e]; i < env_start[e + 1]; ++i) {
             for (int64_t j = i + 1; j < env_start[e + 1]; ++j) {
                 double dx = pos[2 * j] - pos[2 * i], dy = pos[2 * j + 1] - pos[2 * i + 1];
-                double lim = radius[i] + radius[j] - 1e-6;
+                double lim = radius[i] + radius[j] - OR_COLLIDE_DEPTH;
                 if (sqrt(dx * dx + dy * dy) < lim) ++a;
             }
             for (int64_t k = seg_start[e]; k < seg_start[e + 1]; ++k) {
                 double d = sqrt(or_seg_dist2(pos[2 * i], pos[2 * i + 1], segs + 4 * k));
-                if (d < radius[i] - 1e-6) ++s;
+                if (d < radius[i] - OR_COLLIDE_DEPTH) ++s;
             }
         }
         agent_pairs_out[e] = a;

@@ -14,6 +14,11 @@ enum : int {
 };
 
 constexpr int kMaxObstacleLines = 32;
+// Penetration depth (m) from which two agents, or an agent and a segment,
+// count as colliding in the statistics: 1 mm, well above the FP32 resolution
+// of positions (about 4 um at 40 m), so that agents ORCA leaves exactly
+// touching are not counted on rounding noise.
+constexpr float kCollideDepth = 1e-3f;
 // Largest environment the shared-memory-resident kernel takes.
 constexpr int kResidentMaxAgents = 2048;
 // Cell table of the resident kernel: at most kGridMax x kGridMax cells.

@@ -202,36 +202,86 @@ struct StepCtx {
 };
 
 template <int KMAX>
-__device__ __forceinline__ void agent_update(const ResidentArgs& a, const Smem& S, const StepCtx& c, int t,
-                                             double& speed_acc, Tally& w) {
-    const int i = S.sid[t];
-    const float4 me = S.spv[t];
-    const float4 pr = S.par[i];
-    const int K = a.K;
+struct NbList {
+    int id[KMAX];
+    int cnt;
+};
 
-    // ---- A1/A2: K nearest within R, ranked by (FP64 key, index)
-    TopK<KMAX> nb;
-    nb.init();
-    const float R2f = a.R * a.R * (1.0f + 1e-5f);
-    const double Rd = (double)a.R;
+// K nearest agents within R of the agent in sorted slot t, ordered by
+// (FP64 key, index) exactly as the definition ranks them.  Candidates are
+// ranked by their FP32 squared distance (packed with the index into one
+// 64-bit key); FP32 and FP64 keys further apart than kKeyRelErr order alike,
+// so the FP32 order is exact unless two of the first K+1 keys are closer than
+// that, in which case the block is rescanned with FP64 keys.  Candidates
+// within kKeyRelErr of R^2 are admitted by their FP64 key.
+template <int KMAX>
+__device__ __forceinline__ void select_neighbors(const Smem& S, const StepCtx& c, int t, float4 me, float R, int K,
+                                                 NbList<KMAX>& out, Tally& w) {
+    const float R2 = R * R;
+    const float R2hi = R2 * (1.f + kKeyRelErr), R2lo = R2 * (1.f - kKeyRelErr);
+    const double Rd = (double)R;
     const unsigned long long R2bits = (unsigned long long)__double_as_longlong(__dmul_rn(Rd, Rd));
     const double xi = (double)me.x, yi = (double)me.y;
     const int cx = cell_coord(me.x, c.g.x0, c.g.inv_c, c.g.W);
     const int cy = cell_coord(me.y, c.g.y0, c.g.inv_c, c.g.H);
     const int xa = max(cx - 1, 0), xb = min(cx + 1, c.g.W - 1);
-    for (int yy = max(cy - 1, 0); yy <= min(cy + 1, c.g.H - 1); ++yy) {
+    const int ya = max(cy - 1, 0), yb = min(cy + 1, c.g.H - 1);
+    TopK32<KMAX + 1> top;
+    top.init();
+    for (int yy = ya; yy <= yb; ++yy) {
         const int b0 = S.cell[yy * c.g.W + xa], b1 = S.cell[yy * c.g.W + xb + 1];
         w.candidates += (unsigned long long)(b1 - b0);
         for (int u = b0; u < b1; ++u) {
             const float4 o = S.spv[u];
             const float dx = o.x - me.x, dy = o.y - me.y;
             const float d2 = dx * dx + dy * dy;
-            if (d2 < R2f && u != t) {
-                const unsigned long long k = rank_key(xi, yi, o.x, o.y);
-                if (k < R2bits) nb.insert(k, S.sid[u], K);
+            if (d2 < R2hi && u != t) {
+                if (d2 > R2lo && !(rank_key(xi, yi, o.x, o.y) < R2bits)) continue;
+                top.insert(((unsigned long long)__float_as_uint(d2) << 32) | (unsigned)S.sid[u], K + 1);
             }
         }
     }
+    bool near_tie = false;
+#pragma unroll
+    for (int s = 0; s < KMAX; ++s) {
+        if (s < K && s + 1 < top.cnt) {
+            const float ka = TopK32<KMAX + 1>::key_of(top.e[s]), kb = TopK32<KMAX + 1>::key_of(top.e[s + 1]);
+            if (kb - ka <= kKeyRelErr * kb) near_tie = true;
+        }
+    }
+    if (!near_tie) {
+        out.cnt = min(top.cnt, K);
+#pragma unroll
+        for (int s = 0; s < KMAX; ++s) out.id[s] = (int)(unsigned)(top.e[s] & 0xffffffffull);
+        return;
+    }
+    TopK64<KMAX> nb;
+    nb.init();
+    for (int yy = ya; yy <= yb; ++yy) {
+        const int b0 = S.cell[yy * c.g.W + xa], b1 = S.cell[yy * c.g.W + xb + 1];
+        for (int u = b0; u < b1; ++u) {
+            if (u == t) continue;
+            const float4 o = S.spv[u];
+            const unsigned long long k = rank_key(xi, yi, o.x, o.y);
+            if (k < R2bits) nb.insert(k, S.sid[u], K);
+        }
+    }
+    out.cnt = nb.cnt;
+#pragma unroll
+    for (int s = 0; s < KMAX; ++s) out.id[s] = nb.id[s];
+}
+
+template <int KMAX>
+__device__ __forceinline__ void agent_update(const ResidentArgs& a, const Smem& S, const StepCtx& c, int t,
+                                             double& speed_acc, Tally& w) {
+    const int i = S.sid[t];
+    const float4 me = S.spv[t];
+    const float4 pr = S.par[i];
+
+    // ---- A1/A2: K nearest within R, ranked by (FP64 key, index)
+    NbList<KMAX> nb;
+    select_neighbors<KMAX>(S, c, t, me, a.R, a.K, nb, w);
+    const int K = a.K;
     if (c.last && a.nbr_out) {
         int* out = a.nbr_out + (size_t)(c.base + i) * K;
 #pragma unroll
@@ -295,7 +345,10 @@ __device__ __forceinline__ void agent_update(const ResidentArgs& a, const Smem& 
         const int nl = no + nb.cnt;
         int solves = 0, solve_lines = 0;
         const bool feasible = lp2(L, nl, pr.y, pref, v, solves, solve_lines) == nl;
-        if (!feasible) v = lp_fallback(L, nl, no, pr.y, pref);
+        if (!feasible) {
+            Line scratch[KMAX + kMaxObstacleLines];
+            v = lp_fallback(L, nl, no, pr.y, pref, scratch);
+        }
         w.agent_lines += nb.cnt;
         w.obstacle_lines += no;
         w.lp_checks += nl;
@@ -324,7 +377,8 @@ __device__ __forceinline__ void agent_update(const ResidentArgs& a, const Smem& 
 }
 
 // Collision events of the current (post-integration) state: agent pairs
-// i < j closer than r_i + r_j - 1e-6, agents closer than r_i - 1e-6 to a segment.
+// i < j closer than r_i + r_j - kCollideDepth, agents closer than
+// r_i - kCollideDepth to a segment.
 __device__ __forceinline__ void count_collisions(const ResidentArgs& a, const Smem& S, const StepCtx& c, int t,
                                                  unsigned long long& ca, unsigned long long& cs) {
     const int i = S.sid[t];
@@ -340,10 +394,10 @@ __device__ __forceinline__ void count_collisions(const ResidentArgs& a, const Sm
             if (j <= i) continue;
             const float4 o = S.spv[u];
             const float dx = o.x - me.x, dy = o.y - me.y;
-            if (sqrtf(dx * dx + dy * dy) < ri + S.par[j].x - 1e-6f) ++ca;
+            if (sqrtf(dx * dx + dy * dy) < ri + S.par[j].x - kCollideDepth) ++ca;
         }
     }
-    const float lim = ri - 1e-6f;
+    const float lim = ri - kCollideDepth;
     for (int s = 0; s < c.ns; ++s) {
         const float4 sg = __ldg(&a.segs[c.seg0 + s]);
         if (box_dist2(me.x, me.y, sg) >= lim * lim) continue;

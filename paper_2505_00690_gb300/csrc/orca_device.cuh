@@ -3,13 +3,13 @@
 // FP32 throughout, except where a discrete decision or an ill-conditioned
 // quantity must come out as the FP64 definition says:
 //   - the neighbour ranking key (squared distance rounded in FP64 with no
-//     fused multiply-add), so that neighbour lists are bit-exact;
+//     fused multiply-add) for candidates whose FP32 keys are too close to
+//     order, so that neighbour lists are bit-exact;
+//   - near contact, |p|^2 - r^2 in compensated FP32 (FP64 within 1e-6);
 //   - the leg choice (sign of det(p, w)) and the colliding test
 //     (|p|^2 <= r^2) when the FP32 value is within its rounding error of 0;
 //   - the near-parallel test of two LP lines (|det| <= 1e-9) and the
-//     intersection parameter when |det| is small;
-//   - the infeasible-LP fallback (min-max penetration, then the point closest
-//     to the preferred velocity).
+//     intersection parameter when |det| is small.
 // The geometry is that of ORCA (van den Berg et al., ISRR 2011), the
 // collision-avoidance rule the paper uses for its dynamic agents (Sec. 3.2).
 #pragma once
@@ -51,19 +51,20 @@ __device__ __forceinline__ unsigned long long rank_key(double xi, double yi, flo
     return (unsigned long long)__double_as_longlong(k);
 }
 
-// Sorted list of the KMAX smallest (key, id) pairs; only the first K slots
-// (runtime K <= KMAX) are used.  All indices are compile-time so that the
-// list lives in registers.
-template <int KMAX>
-struct TopK {
-    unsigned long long key[KMAX];
-    int id[KMAX];
+// Sorted list of the CAP smallest (FP64 key, id) pairs; only the first K
+// slots (runtime K <= CAP) are used.  All indices are compile-time so that
+// the list lives in registers.  Used when FP32 keys cannot order the
+// candidates (near ties), see select_neighbors.
+template <int CAP>
+struct TopK64 {
+    unsigned long long key[CAP];
+    int id[CAP];
     int cnt;
 
     __device__ __forceinline__ void init() {
         cnt = 0;
 #pragma unroll
-        for (int s = 0; s < KMAX; ++s) {
+        for (int s = 0; s < CAP; ++s) {
             key[s] = ~0ull;
             id[s] = 0x7fffffff;
         }
@@ -71,21 +72,19 @@ struct TopK {
     __device__ __forceinline__ static bool less(unsigned long long ka, int ia, unsigned long long kb, int ib) {
         return ka < kb || (ka == kb && ia < ib);
     }
-    // Insert (k, j) if it ranks among the first K.
     __device__ __forceinline__ void insert(unsigned long long k, int j, int K) {
         if (K <= 0) return;
-        // the last used slot holds the current K-th element (or the sentinel)
         unsigned long long lk = ~0ull;
         int li = 0x7fffffff;
 #pragma unroll
-        for (int s = 0; s < KMAX; ++s)
+        for (int s = 0; s < CAP; ++s)
             if (s == K - 1) { lk = key[s]; li = id[s]; }
         if (!less(k, j, lk, li)) return;
-        int p = 0;  // insertion position = number of entries ranking before (k, j)
+        int p = 0;
 #pragma unroll
-        for (int s = 0; s < KMAX; ++s) p += (s < cnt && less(key[s], id[s], k, j)) ? 1 : 0;
+        for (int s = 0; s < CAP; ++s) p += (s < cnt && less(key[s], id[s], k, j)) ? 1 : 0;
 #pragma unroll
-        for (int s = KMAX - 1; s >= 1; --s) {
+        for (int s = CAP - 1; s >= 1; --s) {
             if (s > p) { key[s] = key[s - 1]; id[s] = id[s - 1]; }
             else if (s == p) { key[s] = k; id[s] = j; }
         }
@@ -94,7 +93,145 @@ struct TopK {
     }
 };
 
+// Sorted list of the CAP smallest packed (FP32 key bits << 32 | id) values:
+// one 64-bit compare orders by key then id (keys are non-negative floats,
+// whose bit patterns order like their values).
+template <int CAP>
+struct TopK32 {
+    unsigned long long e[CAP];
+    int cnt;
+
+    __device__ __forceinline__ void init() {
+        cnt = 0;
+#pragma unroll
+        for (int s = 0; s < CAP; ++s) e[s] = ~0ull;
+    }
+    // Keep the `keep` smallest (keep <= CAP).
+    __device__ __forceinline__ void insert(unsigned long long x, int keep) {
+        unsigned long long last = ~0ull;
+#pragma unroll
+        for (int s = 0; s < CAP; ++s)
+            if (s == keep - 1) last = e[s];
+        if (keep <= 0 || x >= last) return;
+        int p = 0;
+#pragma unroll
+        for (int s = 0; s < CAP; ++s) p += (s < cnt && e[s] < x) ? 1 : 0;
+#pragma unroll
+        for (int s = CAP - 1; s >= 1; --s) {
+            if (s > p) e[s] = e[s - 1];
+            else if (s == p) e[s] = x;
+        }
+        if (p == 0) e[0] = x;
+        cnt = cnt < keep ? cnt + 1 : keep;
+    }
+    __device__ __forceinline__ static float key_of(unsigned long long x) { return __uint_as_float((unsigned)(x >> 32)); }
+};
+
+// Relative error bound of the FP32 squared distance against the FP64
+// ranking key (a few units of 2^-24, with margin): FP32 keys further apart
+// than this order exactly like the FP64 keys.
+constexpr float kKeyRelErr = 1e-6f;
+
 // ---------------------------------------------------------------- A3 ----
+// s + e = a + b exactly (Knuth's two-sum).
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
+// (pj - pi)^2 - (ri + rj)^2 in compensated FP32: the differences and the sum
+// are split into exact two-float pairs, the squares into product + FMA
+// residual, and the cancelling sum is carried with its error terms, so the
+// result is accurate to a few units in its last place even at contact.
+__device__ __forceinline__ float contact_gap2(float pix, float piy, float pjx, float pjy, float ri, float rj) {
+    float xh, xl, yh, yl, rh, rl;
+    two_sum(pjx, -pix, xh, xl);
+    two_sum(pjy, -piy, yh, yl);
+    two_sum(ri, rj, rh, rl);
+    const float h1 = xh * xh, l1 = fmaf(xh, xh, -h1) + 2.f * xh * xl;
+    const float h2 = yh * yh, l2 = fmaf(yh, yh, -h2) + 2.f * yh * yl;
+    const float h3 = rh * rh, l3 = fmaf(rh, rh, -h3) + 2.f * rh * rl;
+    float s, e1, t, e2;
+    two_sum(h1, h2, s, e1);
+    two_sum(s, -h3, t, e2);
+    return t + (((e1 + e2) + (l1 + l2)) - l3);
+}
+
+// FP64 evaluation of the agent half-plane (same geometry as agent_line),
+// used for pairs within a relative 1e-6 of contact.  Every product and sum is rounded
+// separately so that the colliding and leg decisions match an FP64
+// evaluation of the definition exactly.
+__device__ __noinline__ Line agent_line_fp64(float pix, float piy, float vix, float viy, float ri, float pjx,
+                                             float pjy, float vjx, float vjy, float rj, float tau, float dt,
+                                             float alpha, bool i_before_j) {
+    const double px = __dsub_rn((double)pjx, (double)pix), py = __dsub_rn((double)pjy, (double)piy);
+    const double vx = __dsub_rn((double)vix, (double)vjx), vy = __dsub_rn((double)viy, (double)vjy);
+    const double r = __dadd_rn((double)ri, (double)rj);
+    const double dist2 = __dadd_rn(__dmul_rn(px, px), __dmul_rn(py, py));
+    const double r2 = __dmul_rn(r, r);
+    const double T = (double)tau, D = (double)dt;
+    double ux, uy, nx, ny;
+    if (dist2 > r2) {
+        const double wx = __dsub_rn(vx, __ddiv_rn(px, T)), wy = __dsub_rn(vy, __ddiv_rn(py, T));
+        const double w2 = __dadd_rn(__dmul_rn(wx, wx), __dmul_rn(wy, wy));
+        const double wp = __dadd_rn(__dmul_rn(wx, px), __dmul_rn(wy, py));
+        if (wp < 0.0 && __dmul_rn(wp, wp) > __dmul_rn(r2, w2)) {
+            const double wl = sqrt(w2);
+            const double wnx = wx / wl, wny = wy / wl;
+            const double m = r / T - wl;
+            ux = m * wnx;
+            uy = m * wny;
+            nx = wnx;
+            ny = wny;
+        } else {
+            const double leg = sqrt(dist2 - r2);
+            const bool left = __dsub_rn(__dmul_rn(px, wy), __dmul_rn(py, wx)) > 0.0;
+            double lx, ly;
+            if (left) {
+                lx = (px * leg - py * r) / dist2;
+                ly = (px * r + py * leg) / dist2;
+                nx = -ly;
+                ny = lx;
+            } else {
+                lx = (px * leg + py * r) / dist2;
+                ly = (-px * r + py * leg) / dist2;
+                nx = ly;
+                ny = -lx;
+            }
+            const double s = vx * lx + vy * ly;
+            ux = s * lx - vx;
+            uy = s * ly - vy;
+        }
+    } else {
+        const double wx = __dsub_rn(vx, __ddiv_rn(px, D)), wy = __dsub_rn(vy, __ddiv_rn(py, D));
+        const double wl = sqrt(wx * wx + wy * wy);
+        double wnx, wny;
+        if (wl > 0.0) {
+            wnx = wx / wl;
+            wny = wy / wl;
+        } else if (dist2 > 0.0) {
+            const double pl = sqrt(dist2);
+            wnx = -px / pl;
+            wny = -py / pl;
+        } else {
+            wnx = i_before_j ? 1.0 : -1.0;
+            wny = 0.0;
+        }
+        const double m = r / D - wl;
+        ux = m * wnx;
+        uy = m * wny;
+        nx = wnx;
+        ny = wny;
+    }
+    Line L;
+    L.qx = (float)((double)vix + (double)alpha * ux);
+    L.qy = (float)((double)viy + (double)alpha * uy);
+    L.nx = (float)nx;
+    L.ny = (float)ny;
+    return L;
+}
+
 // Reciprocal half-plane of agent i against agent j (current velocities):
 // u = (nearest point of the boundary of the truncated velocity obstacle to
 // v = v_i - v_j) - v, n = the outward normal there, line through v_i + alpha u.
@@ -106,13 +243,17 @@ __device__ __forceinline__ Line agent_line(float pix, float piy, float vix, floa
     const float r = ri + rj;
     const float dist2 = px * px + py * py;
     const float r2 = r * r;
-    bool apart = dist2 > r2;
-    if (fabsf(dist2 - r2) <= 1e-5f * r2) {
-        // too close to call in FP32: decide as FP64 does
-        double dpx = (double)pjx - (double)pix, dpy = (double)pjy - (double)piy;
-        double dr = (double)ri + (double)rj;
-        apart = __dadd_rn(__dmul_rn(dpx, dpx), __dmul_rn(dpy, dpy)) > __dmul_rn(dr, dr);
+    // gap2 = |p|^2 - r^2: near contact it cancels, so there it is evaluated in
+    // compensated FP32 (the colliding test and the legs' length depend on it)
+    float gap2 = dist2 - r2;
+    if (fabsf(gap2) <= 1e-2f * r2) {
+        gap2 = contact_gap2(pix, piy, pjx, pjy, ri, rj);
+        if (fabsf(gap2) <= 1e-6f * r2) {
+            // closer to contact than compensated FP32 can decide like FP64
+            return agent_line_fp64(pix, piy, vix, viy, ri, pjx, pjy, vjx, vjy, rj, tau, dt, alpha, i_before_j);
+        }
     }
+    const bool apart = gap2 > 0.f;
     float ux, uy, nx, ny;
     if (apart) {
         const float inv_tau = __frcp_rn(tau);
@@ -131,7 +272,7 @@ __device__ __forceinline__ Line agent_line(float pix, float piy, float vix, floa
             ny = wny;
         } else {
             // nearest boundary point on a leg (ray from 0 tangent to D(p, r))
-            const float leg = sqrtf(dist2 - r2);
+            const float leg = sqrtf(gap2);
             const float inv_d2 = __frcp_rn(dist2);
             float det = px * wy - py * wx;
             const float scale = fabsf(px * wy) + fabsf(py * wx);
@@ -192,15 +333,38 @@ __device__ __forceinline__ Line agent_line(float pix, float piy, float vix, floa
 }
 
 // ---------------------------------------------------------------- A4 ----
-// Squared distance from p to the segment (a, b) and the closest point.
+// a*d - b*c with one rounding's worth of error (Kahan's FMA scheme).
+__device__ __forceinline__ float det2(float a, float b, float c, float d) {
+    const float w = b * c;
+    const float e = fmaf(-b, c, w);
+    const float f = fmaf(a, d, -w);
+    return f + e;
+}
+
+// Squared distance from p to the segment (a, b) and the closest point,
+// relative to p, so that its rounding error scales with the distance and not
+// with the coordinates or the segment length: inside the segment the closest
+// point is det(a - p, e) / |e|^2 * (e_y, -e_x), the perpendicular foot, with
+// the determinant evaluated by Kahan's scheme.  A clamped projection returns
+// the endpoint itself, so that two segments meeting at a vertex give
+// bit-identical closest points (and lines).
 __device__ __forceinline__ float seg_dist2(float px, float py, float4 s, float& cx, float& cy) {
+    const float ax = s.x - px, ay = s.y - py;
     const float ex = s.z - s.x, ey = s.w - s.y;
-    float t = __fdiv_rn((px - s.x) * ex + (py - s.y) * ey, ex * ex + ey * ey);
-    t = fminf(fmaxf(t, 0.f), 1.f);
-    cx = s.x + t * ex;
-    cy = s.y + t * ey;
-    const float dx = cx - px, dy = cy - py;
-    return dx * dx + dy * dy;
+    const float e2 = ex * ex + ey * ey;
+    const float t = __fdiv_rn(-(ax * ex + ay * ey), e2);
+    if (t <= 0.f) {
+        cx = ax;
+        cy = ay;
+    } else if (t >= 1.f) {
+        cx = s.z - px;
+        cy = s.w - py;
+    } else {
+        const float k = __fdiv_rn(det2(ax, ay, ex, ey), e2);
+        cx = k * ey;
+        cy = -k * ex;
+    }
+    return cx * cx + cy * cy;
 }
 
 // Half-plane of an agent against a static segment, full responsibility: the
@@ -211,14 +375,14 @@ __device__ __forceinline__ float seg_dist2(float px, float py, float4 s, float& 
 // normal of a->b when undecided).
 __device__ __forceinline__ Line obstacle_line(float px, float py, float vx, float vy, float r, float vmax,
                                               float4 s, float tau_o, float dt) {
-    float cx, cy;
+    float cx, cy;  // closest point relative to p
     const float d2 = seg_dist2(px, py, s, cx, cy);
     const float d = sqrtf(d2);
     float mx, my;
     if (d > 0.f) {
         const float inv = __frcp_rn(d);
-        mx = (cx - px) * inv;
-        my = (cy - py) * inv;
+        mx = cx * inv;
+        my = cy * inv;
     } else {
         const float ex = s.z - s.x, ey = s.w - s.y;
         const float inv = rsqrtf(ex * ex + ey * ey);
@@ -242,21 +406,35 @@ __device__ __forceinline__ Line obstacle_line(float px, float py, float vx, floa
 }
 
 // ---------------------------------------------------------------- A5 ----
-// Minimise |v - pref| on line k inside the speed disk and lines 0..k-1.
-__device__ __forceinline__ bool lp1(const Line* L, int k, float vmax, float2 pref, float2& v) {
+// Slack of the FP32 interval tests, in m/s: an interval that comes out empty
+// by less than this (a line touching the speed disk, three lines through one
+// point) is taken as the single point it is in exact arithmetic, instead of
+// sending an LP that FP32 rounding alone made infeasible to the fallback.
+constexpr float kIntervalSlack = 1e-5f;
+
+// Interval [tl, tr] of the parameter t along line k (point q_k + t d_k,
+// d_k = (-n_y, n_x)) inside the speed disk and the lines 0..k-1; false if
+// empty by more than kIntervalSlack.  Near-parallel pairs (|det| < 1e-4 in
+// FP32) are classified and intersected in FP64, parallel meaning
+// |det| <= 1e-9.
+__device__ __forceinline__ bool line_interval(const Line* L, int k, float vmax, float& tl, float& tr) {
     const Line lk = L[k];
-    const float dx = -lk.ny, dy = lk.nx;  // direction along line k
+    const float dx = -lk.ny, dy = lk.nx;
     const float qd = lk.qx * dx + lk.qy * dy;
-    const float disc = qd * qd - (lk.qx * lk.qx + lk.qy * lk.qy) + vmax * vmax;
-    if (disc < 0.f) return false;
+    float disc = qd * qd - (lk.qx * lk.qx + lk.qy * lk.qy) + vmax * vmax;
+    if (disc < 0.f) {
+        // the line misses the disk by about -disc / (2 vmax)
+        if (disc < -2.f * kIntervalSlack * vmax) return false;
+        disc = 0.f;
+    }
     const float sq = sqrtf(disc);
-    float tl = -qd - sq, tr = -qd + sq;
+    tl = -qd - sq;
+    tr = -qd + sq;
     for (int l = 0; l < k; ++l) {
         const Line ll = L[l];
         const float den = dx * ll.nx + dy * ll.ny;  // det(n_k, n_l)
         const float num = (ll.qx - lk.qx) * ll.nx + (ll.qy - lk.qy) * ll.ny;
         if (fabsf(den) < 1e-4f) {
-            // near-parallel: classify and intersect in FP64
             const double ddx = -(double)lk.ny, ddy = (double)lk.nx;
             const double dden = ddx * (double)ll.nx + ddy * (double)ll.ny;
             const double dnum = ((double)ll.qx - (double)lk.qx) * (double)ll.nx +
@@ -273,8 +451,20 @@ __device__ __forceinline__ bool lp1(const Line* L, int k, float vmax, float2 pre
             if (den > 0.f) tl = fmaxf(tl, t);
             else tr = fminf(tr, t);
         }
-        if (tl > tr) return false;
+        if (tl > tr) {
+            if (tl - tr > kIntervalSlack) return false;
+            tl = tr = 0.5f * (tl + tr);
+        }
     }
+    return true;
+}
+
+// Minimise |v - pref| on line k inside the speed disk and lines 0..k-1.
+__device__ __forceinline__ bool lp1(const Line* L, int k, float vmax, float2 pref, float2& v) {
+    float tl, tr;
+    if (!line_interval(L, k, vmax, tl, tr)) return false;
+    const Line lk = L[k];
+    const float dx = -lk.ny, dy = lk.nx;
     float t = (pref.x - lk.qx) * dx + (pref.y - lk.qy) * dy;
     t = fminf(fmaxf(t, tl), tr);
     v.x = lk.qx + t * dx;
@@ -307,163 +497,76 @@ __device__ __forceinline__ int lp2(const Line* L, int n, float vmax, float2 pref
     return n;
 }
 
-// ---------------------------------------------------------------- A5 fallback (FP64) ----
-struct DLine {
-    double qx, qy, nx, ny;
-};
-
-// Line k of the FP64 problems: the FP32 line k as is (k < n_hard), or shifted
-// outward by `shift` (agent lines, relaxed to viol_k <= shift).
-__device__ __forceinline__ DLine shifted_line(const Line* L, int k, int n_hard, double shift) {
-    const Line l = L[k];
-    DLine d{(double)l.qx, (double)l.qy, (double)l.nx, (double)l.ny};
-    if (k >= n_hard) {
-        d.qx -= shift * d.nx;
-        d.qy -= shift * d.ny;
-    }
-    return d;
-}
-
-// Line m of the directional subproblem of agent line i: hard lines first,
-// then for each agent line j in [n_hard, i) the half-plane viol_j <= viol_i,
-// i.e. v.(n_j - n_i) >= q_j.n_j - q_i.n_i.  `valid` is false when n_j ~ n_i
-// (the constraint cannot bind at the optimum then).
-__device__ __forceinline__ DLine sub_line(const Line* L, int n_hard, int i, int m, bool& valid) {
-    valid = true;
-    if (m < n_hard) return shifted_line(L, m, n_hard, 0.0);
-    const Line a = L[i], b = L[m];  // agent line m < i
-    const double nx = (double)b.nx - (double)a.nx, ny = (double)b.ny - (double)a.ny;
-    const double c = ((double)b.qx * b.nx + (double)b.qy * b.ny) - ((double)a.qx * a.nx + (double)a.qy * a.ny);
-    const double nl = sqrt(nx * nx + ny * ny);
-    if (nl < 1e-12) {
-        valid = false;
-        return DLine{0, 0, 1, 0};
-    }
-    const double inx = nx / nl, iny = ny / nl, off = c / nl;
-    return DLine{off * inx, off * iny, inx, iny};
-}
-
-// 1D step shared by the FP64 LPs: interval of line `lk` inside the disk and
-// the previous lines given by `prev(l, valid)`.
-template <class Prev>
-__device__ __forceinline__ bool interval_d(const DLine& lk, int k, double vmax, Prev prev, double& tl, double& tr) {
-    const double dx = -lk.ny, dy = lk.nx;
-    const double qd = lk.qx * dx + lk.qy * dy;
-    const double disc = qd * qd - (lk.qx * lk.qx + lk.qy * lk.qy) + vmax * vmax;
-    if (disc < 0.0) return false;
-    const double sq = sqrt(disc);
-    tl = -qd - sq;
-    tr = -qd + sq;
-    for (int l = 0; l < k; ++l) {
-        bool valid;
-        const DLine ll = prev(l, valid);
-        if (!valid) continue;
-        const double den = dx * ll.nx + dy * ll.ny;
-        const double num = (ll.qx - lk.qx) * ll.nx + (ll.qy - lk.qy) * ll.ny;
-        if (fabs(den) <= kEpsParallel) {
-            if (num > 0.0) return false;
-            continue;
-        }
-        const double t = num / den;
-        if (den > 0.0) tl = fmax(tl, t);
-        else tr = fmin(tr, t);
-        if (tl > tr) return false;
-    }
-    return true;
-}
-
-// Least-distance FP64 LP over lines 0..n-1 (agent lines shifted by `shift`).
-__device__ __forceinline__ bool lp2_d(const Line* L, int n, int n_hard, double shift, double vmax, double px,
-                                      double py, double& vx, double& vy) {
-    const double pl2 = px * px + py * py;
-    if (pl2 > vmax * vmax) {
-        const double k = vmax / sqrt(pl2);
-        vx = px * k;
-        vy = py * k;
-    } else {
-        vx = px;
-        vy = py;
-    }
-    for (int k = 0; k < n; ++k) {
-        const DLine lk = shifted_line(L, k, n_hard, shift);
-        if ((vx - lk.qx) * lk.nx + (vy - lk.qy) * lk.ny < 0.0) {
-            double tl, tr;
-            auto prev = [&](int l, bool& valid) {
-                valid = true;
-                return shifted_line(L, l, n_hard, shift);
-            };
-            if (!interval_d(lk, k, vmax, prev, tl, tr)) return false;
-            const double dx = -lk.ny, dy = lk.nx;
-            double t = (px - lk.qx) * dx + (py - lk.qy) * dy;
-            t = fmin(fmax(t, tl), tr);
-            vx = lk.qx + t * dx;
-            vy = lk.qy + t * dy;
+// ---------------------------------------------------------------- A5 fallback ----
+// Maximise v.o over the speed disk and lines 0..m-1 (incremental, like lp2
+// with a linear objective).  When the objective is perpendicular to the line
+// the optimum lies on (|d.o| <= 1e-6), every point of the interval is
+// optimal and the one closest to pref is taken.
+__device__ __forceinline__ bool lp_dir(const Line* S, int m, float vmax, float ox, float oy, float2 pref, float2& v) {
+    v = make_float2(vmax * ox, vmax * oy);
+    for (int k = 0; k < m; ++k) {
+        const Line lk = S[k];
+        if ((v.x - lk.qx) * lk.nx + (v.y - lk.qy) * lk.ny < 0.f) {
+            float tl, tr;
+            if (!line_interval(S, k, vmax, tl, tr)) return false;
+            const float dx = -lk.ny, dy = lk.nx;
+            const float dd = dx * ox + dy * oy;
+            float t;
+            if (dd > 1e-6f) t = tr;
+            else if (dd < -1e-6f) t = tl;
+            else t = fminf(fmaxf((pref.x - lk.qx) * dx + (pref.y - lk.qy) * dy, tl), tr);
+            v.x = lk.qx + t * dx;
+            v.y = lk.qy + t * dy;
         }
     }
     return true;
 }
 
-// Directional FP64 LP: maximise v.(ox, oy) over the disk and the
-// subproblem lines of agent line i.
-__device__ __forceinline__ bool lp_dir_d(const Line* L, int n_hard, int i, double vmax, double ox, double oy,
-                                         double& vx, double& vy) {
-    vx = vmax * ox;
-    vy = vmax * oy;
-    for (int k = 0; k < i; ++k) {  // hard lines, then agent lines before i
-        bool valid;
-        const DLine lk = sub_line(L, n_hard, i, k, valid);
-        if (!valid) continue;
-        if ((vx - lk.qx) * lk.nx + (vy - lk.qy) * lk.ny < 0.0) {
-            double tl, tr;
-            auto prev = [&](int l, bool& v) { return sub_line(L, n_hard, i, l, v); };
-            if (!interval_d(lk, k, vmax, prev, tl, tr)) return false;
-            const double dx = -lk.ny, dy = lk.nx;
-            const double t = (dx * ox + dy * oy) > 0.0 ? tr : tl;
-            vx = lk.qx + t * dx;
-            vy = lk.qy + t * dy;
-        }
-    }
-    return true;
-}
-
-// Fallback for an infeasible LP (FP64).  Lines [0, n_hard) are static
-// (hard), the rest agent lines (soft).  If the disk and the hard lines leave
-// nothing, all lines are soft.  d* = min over the hard region of the largest
-// agent-line penetration, found by an incremental 3D LP (one directional 2D
-// LP per line that the current point violates by more than the current d);
-// the result is the point closest to pref with every penetration <= d*.
-__device__ __forceinline__ float2 lp_fallback(const Line* L, int n, int n_hard, float vmax_f, float2 pref) {
-    const double vmax = vmax_f, px = pref.x, py = pref.y;
-    double vx, vy;
-    if (!lp2_d(L, n_hard, n_hard, 0.0, vmax, px, py, vx, vy)) {
+// Fallback for an infeasible LP.  Lines [0, n_hard) are static (hard), the
+// rest agent lines (soft), penetration viol_k(v) = -(v - q_k).n_k.  If the
+// disk and the hard lines leave nothing, all lines are soft.  The velocity of
+// least maximal penetration is found by an incremental 3D LP over (v, t):
+// while the current point penetrates agent line i by more than the current
+// maximum, the optimum moves onto viol_i = t, where it maximises v.n_i subject
+// to the hard lines and viol_j <= viol_i (j < i), i.e. the half-planes
+// v.(n_j - n_i) >= q_j.n_j - q_i.n_i.  The least-penetration point is
+// unique except when that subproblem's optimum is a whole interval, where
+// lp_dir takes the point closest to pref.  S is scratch for the subproblem
+// lines (at least n entries).
+__device__ __forceinline__ float2 lp_fallback(const Line* L, int n, int n_hard, float vmax, float2 pref, Line* S) {
+    float2 v;
+    int solves = 0, solve_lines = 0;
+    if (lp2(L, n_hard, vmax, pref, v, solves, solve_lines) < n_hard) {
         n_hard = 0;
-        const double pl2 = px * px + py * py;
-        const double k = pl2 > vmax * vmax ? vmax / sqrt(pl2) : 1.0;
-        vx = px * k;
-        vy = py * k;
+        const float pl2 = pref.x * pref.x + pref.y * pref.y;
+        const float k = pl2 > vmax * vmax ? vmax * rsqrtf(pl2) : 1.f;
+        v = make_float2(pref.x * k, pref.y * k);
     }
-    double dist = -1e300;
+    float dist = -INFINITY;
     for (int i = n_hard; i < n; ++i) {
         const Line li = L[i];
-        const double viol = -((vx - li.qx) * li.nx + (vy - li.qy) * li.ny);
-        if (viol > dist + 1e-12) {
-            double tx, ty;
-            if (lp_dir_d(L, n_hard, i, vmax, (double)li.nx, (double)li.ny, tx, ty)) {
-                vx = tx;
-                vy = ty;
+        const float viol = -((v.x - li.qx) * li.nx + (v.y - li.qy) * li.ny);
+        if (viol > dist) {
+            int m = 0;
+            for (int k = 0; k < n_hard; ++k) S[m++] = L[k];
+            const float ci = li.qx * li.nx + li.qy * li.ny;
+            for (int j = n_hard; j < i; ++j) {
+                const Line lj = L[j];
+                float nx = lj.nx - li.nx, ny = lj.ny - li.ny;
+                const float nl2 = nx * nx + ny * ny;
+                if (nl2 < 1e-12f) continue;  // same direction: cannot bind at the optimum
+                const float inv = rsqrtf(nl2);
+                nx *= inv;
+                ny *= inv;
+                const float c = ((lj.qx * lj.nx + lj.qy * lj.ny) - ci) * inv;
+                S[m++] = Line{c * nx, c * ny, nx, ny};
             }
-            dist = -((vx - li.qx) * li.nx + (vy - li.qy) * li.ny);
+            float2 t;
+            if (lp_dir(S, m, vmax, li.nx, li.ny, pref, t)) v = t;
+            dist = -((v.x - li.qx) * li.nx + (v.y - li.qy) * li.ny);
         }
     }
-    // d* at the point found, then the closest point to pref within it
-    double dstar = 0.0;
-    for (int k = n_hard; k < n; ++k) {
-        const Line lk = L[k];
-        dstar = fmax(dstar, -((vx - lk.qx) * lk.nx + (vy - lk.qy) * lk.ny));
-    }
-    double rx, ry;
-    if (lp2_d(L, n, n_hard, dstar + 1e-10, vmax, px, py, rx, ry)) return make_float2((float)rx, (float)ry);
-    return make_float2((float)vx, (float)vy);
+    return v;
 }
 
 }  // namespace crowd

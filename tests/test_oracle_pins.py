@@ -595,9 +595,9 @@ def test_no_overlap_guarantee():
 
 
 def test_collision_counter_hand_case():
-    sc = one_env([[0, 0], [0.5, 0], [3, 0]], [[0, 0]] * 3, [[0, 0]] * 3, 0.3, 1.0,
-                 segs=[(2.8, -1, 2.8, 1)])
+    sc = one_env([[0, 0], [0.5, 0], [3, 0], [10, 0], [10.5995, 0], [20, 0]], [[0, 0]] * 6, [[0, 0]] * 6, 0.3, 1.0,
+                 segs=[(2.8, -1, 2.8, 1), (20.2995, -1, 20.2995, 1)])
     o = oracle.OracleScene(sc)
     a, s = o.collisions(sc.pos.astype(np.float64))
-    assert a[0] == 1  # agents 0 and 1 overlap (0.5 < 0.6)
-    assert s[0] == 1  # agent 2 is 0.2 from the segment (< 0.3)
+    assert a[0] == 1  # agents 0 and 1 overlap by 0.1 m; 3 and 4 by 0.5 mm only (below the 1 mm depth)
+    assert s[0] == 1  # agent 2 is 0.2 from a segment (< 0.3); agent 5 penetrates the other by 0.5 mm only
