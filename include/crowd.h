@@ -71,7 +71,9 @@ enum { CROWD_HOST = 0, CROWD_DEVICE = 1 };
 enum {
     CROWD_FLAG_EXPORT_NEIGHBORS = 1, /* keep the neighbour lists of the last step (crowd_read_neighbors) */
     CROWD_FLAG_STATS = 2,            /* accumulate rollout statistics (crowd_read_stats) */
-    CROWD_FLAG_COUNT_WORK = 4        /* count the algorithm's work items (crowd_read_work) */
+    CROWD_FLAG_COUNT_WORK = 4,       /* count the algorithm's work items (crowd_read_work) */
+    CROWD_FLAG_FORCE_TILED = 8       /* run every environment on the tiled (global-memory) path; by
+                                        default only environments of more than 2048 agents do */
 };
 
 /* Work counters (CROWD_FLAG_COUNT_WORK), summed over all agents and steps

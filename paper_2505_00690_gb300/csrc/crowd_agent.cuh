@@ -1,0 +1,254 @@
+// One agent's crowd update (steps A2-A6), shared by the kernels.
+//
+// The kernels differ only in where candidates and neighbour states live
+// (shared memory for an environment resident in one CTA, global memory for
+// large environments); they pass that in as small accessor objects:
+//   Src    (candidates, in cell order):
+//            int2 row(yy, xa, xb)   sorted-slot range of cells xa..xb of row yy
+//            float4 cand(u)         (px, py, vx, vy) of sorted slot u
+//            int cand_id(u)         environment-local index of sorted slot u
+//   Agents (neighbour lookup by environment-local index):
+//            float4 state(j)        (px, py, vx, vy), robot velocity = command
+//            float radius(j)
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "crowd_internal.h"
+#include "orca_device.cuh"
+
+namespace crowd {
+
+// Agents whose LP was infeasible, queued with their lines for the
+// warp-cooperative fallback (see coop_fallback).
+struct FbEntry {
+    int agent;     // environment-local index
+    int n, n_hard; // lines, of which the first n_hard are static segments
+    float vmax;
+    float2 pref;
+    float4 me;     // step-start state
+};
+struct FbQueue {
+    int* count;
+    int cap, lmax;
+    FbEntry* entries;
+    Line* pool;  // cap x lmax lines
+    __device__ __forceinline__ bool push(const Line* L, int n, int n_hard, float vmax, float2 pref, int agent,
+                                         float4 me) const {
+        const int slot = atomicAdd(count, 1);
+        if (slot >= cap) return false;
+        Line* dst = pool + (size_t)slot * lmax;
+        for (int k = 0; k < n; ++k) dst[k] = L[k];
+        entries[slot] = FbEntry{agent, n, n_hard, vmax, pref, me};
+        return true;
+    }
+};
+
+// Per-thread work tallies (only reported when counting is on).
+struct Tally {
+    unsigned long long agent_steps = 0, candidates = 0, agent_lines = 0, obstacle_lines = 0, segment_tests = 0,
+                       lp_checks = 0, lp_solves = 0, lp_solve_lines = 0, fallbacks = 0;
+};
+
+template <int KMAX>
+struct NbList {
+    int id[KMAX];
+    int cnt;
+};
+
+// Parameters of the step shared by all agents.
+struct AgentParams {
+    float R, dt, tau, tau_o, robot_alpha;
+    int K;
+    const float4* segs;  // segments of all environments
+    int* err;            // device error word
+};
+
+// Distance from p to the bounding box of a segment, squared (a cheap lower
+// bound of the segment distance used to skip far segments).
+__device__ __forceinline__ float box_dist2(float px, float py, float4 s) {
+    const float dx = fmaxf(fmaxf(fminf(s.x, s.z) - px, px - fmaxf(s.x, s.z)), 0.f);
+    const float dy = fmaxf(fmaxf(fminf(s.y, s.w) - py, py - fmaxf(s.y, s.w)), 0.f);
+    return dx * dx + dy * dy;
+}
+
+// A2: the K nearest agents within R of agent `self` (in cell (cx, cy) of a
+// W x H grid with cell size >= R), ordered by (FP64 key, index) exactly as
+// the definition ranks them.  Candidates are ranked by their FP32 squared
+// distance packed with the index into one 64-bit key; FP32 and FP64 keys
+// further apart than kKeyRelErr order alike, so the FP32 order is exact
+// unless two of the first K+1 keys are closer than that, in which case the
+// 3x3 block is rescanned with FP64 keys.  Candidates within kKeyRelErr of R^2
+// are admitted by their FP64 key.
+template <int KMAX, class Src>
+__device__ __forceinline__ void select_neighbors(const Src& src, int cx, int cy, int W, int H, int self, float4 me,
+                                                 float R, int K, NbList<KMAX>& out, Tally& w) {
+    const float R2 = R * R;
+    const float R2hi = R2 * (1.f + kKeyRelErr), R2lo = R2 * (1.f - kKeyRelErr);
+    const double Rd = (double)R;
+    const unsigned long long R2bits = (unsigned long long)__double_as_longlong(__dmul_rn(Rd, Rd));
+    const double xi = (double)me.x, yi = (double)me.y;
+    const int xa = max(cx - 1, 0), xb = min(cx + 1, W - 1);
+    const int ya = max(cy - 1, 0), yb = min(cy + 1, H - 1);
+    TopK32<KMAX + 1> top;
+    top.init();
+    for (int yy = ya; yy <= yb; ++yy) {
+        const int2 r = src.row(yy, xa, xb);
+        w.candidates += (unsigned long long)(r.y - r.x);
+        for (int u = r.x; u < r.y; ++u) {
+            const float4 o = src.cand(u);
+            const float dx = o.x - me.x, dy = o.y - me.y;
+            const float d2 = dx * dx + dy * dy;
+            if (d2 < R2hi) {
+                const int j = src.cand_id(u);
+                if (j == self) continue;
+                if (d2 > R2lo && !(rank_key(xi, yi, o.x, o.y) < R2bits)) continue;
+                top.insert(((unsigned long long)__float_as_uint(d2) << 32) | (unsigned)j, K + 1);
+            }
+        }
+    }
+    bool near_tie = false;
+#pragma unroll
+    for (int s = 0; s < KMAX; ++s) {
+        if (s < K && s + 1 < top.cnt) {
+            const float ka = TopK32<KMAX + 1>::key_of(top.e[s]), kb = TopK32<KMAX + 1>::key_of(top.e[s + 1]);
+            if (kb - ka <= kKeyRelErr * kb) near_tie = true;
+        }
+    }
+    if (!near_tie) {
+        out.cnt = min(top.cnt, K);
+#pragma unroll
+        for (int s = 0; s < KMAX; ++s) out.id[s] = (int)(unsigned)(top.e[s] & 0xffffffffull);
+        return;
+    }
+    TopK64<KMAX> nb;
+    nb.init();
+    for (int yy = ya; yy <= yb; ++yy) {
+        const int2 r = src.row(yy, xa, xb);
+        for (int u = r.x; u < r.y; ++u) {
+            const int j = src.cand_id(u);
+            if (j == self) continue;
+            const float4 o = src.cand(u);
+            const unsigned long long k = rank_key(xi, yi, o.x, o.y);
+            if (k < R2bits) nb.insert(k, j, K);
+        }
+    }
+    out.cnt = nb.cnt;
+#pragma unroll
+    for (int s = 0; s < KMAX; ++s) out.id[s] = nb.id[s];
+}
+
+// Segment candidates of an agent: all segments of its environment, or a
+// precomputed per-cell list (indices relative to the environment's first
+// segment, ascending).
+struct AllSegments {
+    int ns;
+    __device__ __forceinline__ int count() const { return ns; }
+    __device__ __forceinline__ int id(int q) const { return q; }
+};
+struct ListedSegments {
+    const int* ids;
+    int n;
+    __device__ __forceinline__ int count() const { return n; }
+    __device__ __forceinline__ int id(int q) const { return __ldg(&ids[q]); }
+};
+
+// A0, A3-A5: the new velocity of non-robot agent i (environment-local index)
+// with state `me` (px, py, vx, vy), parameters `pr` (r, v_max, preferred
+// speed, 0), goal `gl`, its neighbour list, and the segment candidates
+// `sl` of its environment (whose first segment is seg0).
+// With a queue, an infeasible LP is queued for the warp-cooperative fallback
+// (`queued` set, the returned velocity meaningless); without one, or when it
+// is full, the fallback runs here.
+template <int KMAX, class Agents, class SegList>
+__device__ __forceinline__ float2 solve_velocity(const AgentParams& a, const Agents& ag, int i, int robot, float4 me,
+                                                 float4 pr, float2 gl, int seg0, const SegList& sl,
+                                                 const NbList<KMAX>& nb, Tally& w, const FbQueue* fbq,
+                                                 bool& queued) {
+    queued = false;
+    const float2 pref = pref_velocity(me.x, me.y, gl.x, gl.y, pr.z, a.dt);
+    Line L[KMAX + kMaxObstacleLines];
+
+    // A4: segments within r + tau_o v_max, ordered by (distance^2, id)
+    const float reach = pr.x + a.tau_o * pr.y;
+    const float reach2 = reach * reach;
+    float okey[kMaxObstacleLines];
+    int oid[kMaxObstacleLines];
+    int no = 0;
+    const int ns = sl.count();
+    for (int q = 0; q < ns; ++q) {
+        const int s = sl.id(q);
+        const float4 sg = __ldg(&a.segs[seg0 + s]);
+        if (box_dist2(me.x, me.y, sg) >= reach2) continue;
+        ++w.segment_tests;
+        float qx, qy;
+        const float d2 = seg_dist2(me.x, me.y, sg, qx, qy);
+        if (!(d2 < reach2)) continue;
+        if (no == kMaxObstacleLines) {
+            atomicOr(a.err, kErrObstacleOverflow);
+            if (!(d2 < okey[no - 1])) continue;
+            --no;  // drop the farthest
+        }
+        int p = no;
+        while (p > 0 && okey[p - 1] > d2) {
+            okey[p] = okey[p - 1];
+            oid[p] = oid[p - 1];
+            --p;
+        }
+        okey[p] = d2;
+        oid[p] = s;
+        ++no;
+    }
+    for (int k = 0; k < no; ++k)
+        L[k] = obstacle_line(me.x, me.y, me.z, me.w, pr.x, pr.y, __ldg(&a.segs[seg0 + oid[k]]), a.tau_o, a.dt);
+
+    // A3: one reciprocal half-plane per neighbour, in list order
+#pragma unroll
+    for (int s = 0; s < KMAX; ++s) {
+        if (s < nb.cnt) {
+            const int j = nb.id[s];
+            const float4 o = ag.state(j);
+            const float alpha = (j == robot) ? a.robot_alpha : 0.5f;
+            L[no + s] = agent_line(me.x, me.y, me.z, me.w, pr.x, o.x, o.y, o.z, o.w, ag.radius(j), a.tau, a.dt,
+                                   alpha, i < j);
+        }
+    }
+
+    // A5: LP, fallback when infeasible
+    const int nl = no + nb.cnt;
+    int solves = 0, solve_lines = 0;
+    float2 v;
+    const bool feasible = lp2(L, nl, pr.y, pref, v, solves, solve_lines) == nl;
+    if (!feasible) {
+        if (fbq && fbq->push(L, nl, no, pr.y, pref, i, me)) {
+            queued = true;
+        } else {
+            Line scratch[KMAX + kMaxObstacleLines];
+            v = lp_fallback(L, nl, no, pr.y, pref, scratch);
+        }
+    }
+    w.agent_lines += nb.cnt;
+    w.obstacle_lines += no;
+    w.lp_checks += nl;
+    w.lp_solves += solves;
+    w.lp_solve_lines += solve_lines;
+    w.fallbacks += feasible ? 0 : 1;
+    return v;
+}
+
+// Warp-reduce the tallies and add them to the global counters.
+__device__ __forceinline__ void flush_tally(const Tally& tally, WorkCount* work) {
+    unsigned long long* dst = &work->agent_steps;
+    const unsigned long long vals[9] = {tally.agent_steps, tally.candidates, tally.agent_lines,
+                                        tally.obstacle_lines, tally.segment_tests, tally.lp_checks,
+                                        tally.lp_solves, tally.lp_solve_lines, tally.fallbacks};
+#pragma unroll
+    for (int q = 0; q < 9; ++q) {
+        unsigned long long v = vals[q];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if ((threadIdx.x & 31) == 0 && v) atomicAdd(dst + q, v);
+    }
+}
+
+}  // namespace crowd

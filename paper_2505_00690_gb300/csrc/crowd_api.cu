@@ -88,12 +88,41 @@ struct crowd_ctx {
     EnvStats* stats = nullptr;
     WorkCount* work = nullptr;
 
-    // launch configuration
+    // resident path: environments that fit one CTA (the first n_res of `order`)
+    int n_res = 0;
+    int res_max_agents = 0;
     int block = 0, grid = 0;
 
+    // tiled path: larger environments (or all, with CROWD_FLAG_FORCE_TILED)
+    int n_tiled = 0, tiled_max_agents = 0, tiled_max_tiles = 0, halo_cap = 0;
+    std::vector<TiledEnv> h_tenvs;
+    TiledEnv* tenvs = nullptr;
+    float4* state_b = nullptr;
+    float4* sorted_pv = nullptr;
+    int* key = nullptr;
+    int* rank = nullptr;
+    int* count = nullptr;
+    int* start = nullptr;
+    int* sorted_id = nullptr;
+    int* seg_cell_start = nullptr;
+    int* seg_cell_ids = nullptr;
+    SegGrid* seg_grid = nullptr;
+    long long* d_step = nullptr;
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t graph = nullptr;
+    struct GraphKey {
+        int n_steps = 0;
+        float dt = 0.f;
+        const void* rv = nullptr;
+        bool operator==(const GraphKey& o) const { return n_steps == o.n_steps && dt == o.dt && rv == o.rv; }
+    } gkey;
+
     ~crowd_ctx() {
+        if (graph) cudaGraphExecDestroy(graph);
+        if (cap_stream) cudaStreamDestroy(cap_stream);
         void* ptrs[] = {env_start, seg_start, robot_index, order, queue, err, state, par, goal,
-                        segs, robot_vel, nbr, reach, stats, work};
+                        segs, robot_vel, nbr, reach, stats, work, tenvs, state_b, sorted_pv, key, rank,
+                        count, start, sorted_id, seg_cell_start, seg_cell_ids, seg_grid, d_step};
         for (void* q : ptrs)
             if (q) cudaFree(q);
     }
@@ -129,6 +158,247 @@ crowd_status read_err_word(crowd_t h) {
                         kMaxObstacleLines);
         return fail(CROWD_EDEVICE, "device error word 0x%x", err);
     }
+    return CROWD_OK;
+}
+
+
+// Largest r + tau_obst v_max over an environment's agents, with a margin.
+double seg_reach(int base, int n, const float* radii, const float* vmax, const crowd_params& p) {
+    double reach = 0.0;
+    const double tau_o = p.time_horizon_obst > 0.f ? p.time_horizon_obst : p.time_horizon;
+    for (int i = 0; i < n; ++i) reach = std::max(reach, (double)radii[base + i] + tau_o * (double)vmax[base + i]);
+    return reach * (1.0 + 1e-5) + 1e-6;
+}
+
+// Per-cell segment lists of a W x H grid (origin x0, y0, cell size cc) at
+// offset `off`: segment s is listed in a cell when it comes within
+// reach + half the cell diagonal of the cell's centre, hence within reach of
+// some point of the cell.  Agents clamped into a border cell from outside the
+// grid are covered too as long as the grid contains every segment: clamping
+// onto a box does not increase distances to points inside it.
+void build_seg_lists(const float* segs, int seg0, int ns, double x0, double y0, double cc, int W, int H, double reach,
+                     int off, std::vector<int>& seg_cell_start, std::vector<int>& seg_cell_ids) {
+    const double half_diag = 0.5 * std::sqrt(2.0) * cc;
+    std::vector<std::vector<int>> lists((size_t)W * H);
+    for (int s = 0; s < ns; ++s) {
+        const float* q = segs + 4 * (seg0 + s);
+        const double ax = q[0], ay = q[1], bx = q[2], by = q[3];
+        const int cx0 = std::max(0, (int)std::floor((std::min(ax, bx) - reach - x0) / cc) - 1);
+        const int cx1 = std::min(W - 1, (int)std::floor((std::max(ax, bx) + reach - x0) / cc) + 1);
+        const int cy0 = std::max(0, (int)std::floor((std::min(ay, by) - reach - y0) / cc) - 1);
+        const int cy1 = std::min(H - 1, (int)std::floor((std::max(ay, by) + reach - y0) / cc) + 1);
+        const double ex = bx - ax, ey = by - ay, e2 = ex * ex + ey * ey;
+        for (int cy = cy0; cy <= cy1; ++cy)
+            for (int cx = cx0; cx <= cx1; ++cx) {
+                const double px = x0 + (cx + 0.5) * cc, py = y0 + (cy + 0.5) * cc;
+                double t = ((px - ax) * ex + (py - ay) * ey) / e2;
+                t = std::min(1.0, std::max(0.0, t));
+                const double dx = ax + t * ex - px, dy = ay + t * ey - py;
+                if (std::sqrt(dx * dx + dy * dy) < reach + half_diag) lists[(size_t)cy * W + cx].push_back(s);
+            }
+    }
+    if ((int)seg_cell_start.size() < off + W * H + 1) seg_cell_start.resize(off + W * H + 1);
+    for (size_t k = 0; k < lists.size(); ++k) {
+        seg_cell_start[off + k] = (int)seg_cell_ids.size();
+        seg_cell_ids.insert(seg_cell_ids.end(), lists[k].begin(), lists[k].end());
+    }
+    seg_cell_start[off + lists.size()] = (int)seg_cell_ids.size();
+}
+
+// Segment grid of a resident environment: the bounding box of its segments
+// padded by reach, cells of at least reach/2 and at most 64 a side.
+SegGrid build_seg_grid(int base, int n, int seg0, int ns, const float* radii, const float* vmax, const float* segs,
+                       const crowd_params& p, int off, std::vector<int>& seg_cell_start,
+                       std::vector<int>& seg_cell_ids) {
+    SegGrid g{};
+    g.off = off;
+    if (ns == 0) {
+        g.x0 = g.y0 = 0.f;
+        g.inv_c = 1.f;
+        g.W = g.H = 1;
+        build_seg_lists(segs, seg0, 0, 0.0, 0.0, 1.0, 1, 1, 0.0, off, seg_cell_start, seg_cell_ids);
+        return g;
+    }
+    const double reach = seg_reach(base, n, radii, vmax, p);
+    double x0 = 1e300, y0 = 1e300, x1 = -1e300, y1 = -1e300;
+    for (int s = 0; s < ns; ++s) {
+        const float* q = segs + 4 * (seg0 + s);
+        x0 = std::min({x0, (double)q[0], (double)q[2]});
+        x1 = std::max({x1, (double)q[0], (double)q[2]});
+        y0 = std::min({y0, (double)q[1], (double)q[3]});
+        y1 = std::max({y1, (double)q[1], (double)q[3]});
+    }
+    x0 -= reach;
+    y0 -= reach;
+    x1 += reach;
+    y1 += reach;
+    const double ext = std::max(x1 - x0, y1 - y0);
+    const float c = (float)std::max(std::max(reach * 0.5, 1e-3), ext / 63.0);
+    g.x0 = (float)x0;
+    g.y0 = (float)y0;
+    g.inv_c = std::nextafter(1.0f / c, 0.0f);
+    const double cc = 1.0 / (double)g.inv_c;
+    g.W = std::min(64, (int)((x1 - x0) / cc) + 1);
+    g.H = std::min(64, (int)((y1 - y0) / cc) + 1);
+    build_seg_lists(segs, seg0, ns, x0, y0, cc, g.W, g.H, reach, off, seg_cell_start, seg_cell_ids);
+    return g;
+}
+
+// Static grid of a tiled environment: the bounding box of its agents' start
+// positions and its segments, padded by R, with cells of at least R (times a
+// margin for FP32 rounding of cell coordinates) and at most kTiledGridMax a
+// side; and for every cell the ascending list of the environment's segments
+// that can come within r + tau_obst v_max of a point of the cell.  Agents that
+// leave the box are clamped into its border cells, which keeps both the 3x3
+// neighbour search and the segment lists exact.
+void build_tiled_env(int e, int base, int n, int seg0, int ns, int robot, const float* pos, const float* radii,
+                     const float* vmax, const float* segs, const crowd_params& p, int co, TiledEnv& te,
+                     std::vector<int>& seg_cell_start, std::vector<int>& seg_cell_ids) {
+    const double R = p.neighbor_dist;
+    double x0 = 1e300, y0 = 1e300, x1 = -1e300, y1 = -1e300;
+    for (int i = 0; i < n; ++i) {
+        x0 = std::min(x0, (double)pos[2 * (base + i)]);
+        x1 = std::max(x1, (double)pos[2 * (base + i)]);
+        y0 = std::min(y0, (double)pos[2 * (base + i) + 1]);
+        y1 = std::max(y1, (double)pos[2 * (base + i) + 1]);
+    }
+    for (int s = 0; s < ns; ++s) {
+        const float* q = segs + 4 * (seg0 + s);
+        x0 = std::min({x0, (double)q[0], (double)q[2]});
+        x1 = std::max({x1, (double)q[0], (double)q[2]});
+        y0 = std::min({y0, (double)q[1], (double)q[3]});
+        y1 = std::max({y1, (double)q[1], (double)q[3]});
+    }
+    if (!(x1 >= x0)) x0 = x1 = y0 = y1 = 0.0;
+    x0 -= R;
+    y0 -= R;
+    x1 += R;
+    y1 += R;
+    const double ext = std::max(x1 - x0, y1 - y0);
+    const float c = (float)std::max(R * 1.0001, ext / (kTiledGridMax - 1));
+    te.e = e;
+    te.base = base;
+    te.n = n;
+    te.seg0 = seg0;
+    te.robot = robot;
+    te.co = co;
+    te.x0 = (float)x0;
+    te.y0 = (float)y0;
+    // round toward zero so that the cell size in use is >= c
+    te.inv_c = std::nextafter(1.0f / c, 0.0f);
+    const double cc = 1.0 / (double)te.inv_c;
+    te.W = std::min(kTiledGridMax, (int)((x1 - x0) / cc) + 1);
+    te.H = std::min(kTiledGridMax, (int)((y1 - y0) / cc) + 1);
+
+    build_seg_lists(segs, seg0, ns, x0, y0, cc, te.W, te.H, seg_reach(base, n, radii, vmax, p), co, seg_cell_start,
+                    seg_cell_ids);
+}
+
+
+// Arguments of step s (0-based) of an n-step tiled sequence.
+TiledStepArgs tiled_args(crowd_t h, float dt, const float2* rv, int s, int n_steps, bool stats, float tau_o,
+                         int mode) {
+    TiledStepArgs a{};
+    a.envs = h->tenvs;
+    a.n_envs = h->n_tiled;
+    a.state_in = (s & 1) ? h->state_b : h->state;
+    a.state_out = (s & 1) ? h->state : h->state_b;
+    a.robot_vel = (rv && mode != kTiledStatsOnly) ? rv + (size_t)s * h->E : nullptr;
+    a.par = h->par;
+    a.goal = h->goal;
+    a.segs = h->segs;
+    a.seg_cell_start = h->seg_cell_start;
+    a.seg_cell_ids = h->seg_cell_ids;
+    a.key = h->key;
+    a.rank = h->rank;
+    a.count = h->count;
+    a.start = h->start;
+    a.sorted_pv = h->sorted_pv;
+    a.sorted_id = h->sorted_id;
+    a.halo_cap = h->halo_cap;
+    a.R = h->p.neighbor_dist;
+    a.dt = dt;
+    a.tau = h->p.time_horizon;
+    a.tau_o = tau_o;
+    a.robot_alpha = h->p.robot_responsibility;
+    a.K = h->p.max_neighbors;
+    a.mode = mode;
+    a.nbr_out = (s == n_steps - 1 && mode != kTiledStatsOnly) ? h->nbr : nullptr;
+    a.stats = stats ? h->stats : nullptr;
+    a.reach = h->reach;
+    a.step_index = h->d_step;
+    a.work = mode == kTiledStatsOnly ? nullptr : h->work;
+    a.err = h->err;
+    return a;
+}
+
+// Enqueue an n-step tiled sequence on `s`: the steps alternate between the
+// two state buffers; an odd count ends with the tiled environments copied
+// back; with statistics a last pass counts the collisions of the final state.
+cudaError_t enqueue_tiled(crowd_t h, float dt, const float2* rv, int n_steps, bool stats, float tau_o,
+                          cudaStream_t s) {
+    for (int k = 0; k < n_steps; ++k) {
+        const int mode = (stats && k > 0) ? kTiledStepCount : kTiledStep;
+        cudaError_t e = launch_tiled_step(tiled_args(h, dt, rv, k, n_steps, stats, tau_o, mode), h->tiled_max_agents,
+                                          h->tiled_max_tiles, s);
+        if (e != cudaSuccess) return e;
+    }
+    if (n_steps & 1) {
+        for (const TiledEnv& te : h->h_tenvs) {
+            if (!te.n) continue;
+            cudaError_t e = cudaMemcpyAsync(h->state + te.base, h->state_b + te.base, sizeof(float4) * te.n,
+                                            cudaMemcpyDeviceToDevice, s);
+            if (e != cudaSuccess) return e;
+        }
+    }
+    if (stats) {
+        cudaError_t e = launch_tiled_step(tiled_args(h, dt, nullptr, 0, 1, stats, tau_o, kTiledStatsOnly),
+                                          h->tiled_max_agents, h->tiled_max_tiles, s);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+// Run the tiled environments n steps: a single step is launched directly;
+// longer calls replay a CUDA graph of the whole sequence, captured once per
+// (n_steps, dt, command buffer) and cached.
+crowd_status tiled_steps(crowd_t h, float dt, const float2* rv, int n_steps, bool stats, float tau_o) {
+    cudaError_t e = launch_set_step(h->d_step, h->step_index, h->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "set step index");
+    if (n_steps == 1) {
+        e = enqueue_tiled(h, dt, rv, n_steps, stats, tau_o, h->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "launch tiled step");
+        return CROWD_OK;
+    }
+    crowd_ctx::GraphKey key;
+    key.n_steps = n_steps;
+    key.dt = dt;
+    key.rv = rv;
+    if (!h->graph || !(key == h->gkey)) {
+        if (h->graph) {
+            cudaGraphExecDestroy(h->graph);
+            h->graph = nullptr;
+        }
+        cudaGraph_t g = nullptr;
+        e = cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return cuda_fail(e, "begin graph capture");
+        cudaError_t le = enqueue_tiled(h, dt, rv, n_steps, stats, tau_o, h->cap_stream);
+        e = cudaStreamEndCapture(h->cap_stream, &g);
+        if (le != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            return cuda_fail(le, "capture tiled steps");
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "end graph capture");
+        e = cudaGraphInstantiate(&h->graph, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            h->graph = nullptr;
+            return cuda_fail(e, "instantiate graph");
+        }
+        h->gkey = key;
+    }
+    e = cudaGraphLaunch(h->graph, h->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "launch graph");
     return CROWD_OK;
 }
 
@@ -177,9 +447,6 @@ crowd_status crowd_create(int32_t n_envs, const int32_t* agents_per_env, const f
             return fail(CROWD_EINVAL, "robot_index[%d] out of range", e);
     }
     if (N >= (int64_t)1 << 31 || S >= (int64_t)1 << 31) return fail(CROWD_EINVAL, "too many agents or segments");
-    if (max_agents > kResidentMaxAgents)
-        return fail(CROWD_EINVAL, "an environment has %d agents; at most %d per environment are supported",
-                    max_agents, kResidentMaxAgents);
     if (N > 0 && (!radii || !max_speeds || !init_pos)) return fail(CROWD_EINVAL, "agent arrays are null");
     if (S > 0 && !segments) return fail(CROWD_EINVAL, "segments is null");
     if (!finite_all(init_pos, (size_t)N * 2)) return fail(CROWD_EINVAL, "init_pos holds NaN/Inf");
@@ -216,11 +483,40 @@ crowd_status crowd_create(int32_t n_envs, const int32_t* agents_per_env, const f
         seg_start[e + 1] = seg_start[e] + (segs_per_env ? segs_per_env[e] : 0);
         if (robot_index) robot[e] = robot_index[e];
     }
-    // largest environments first: the queue then balances uneven batches
-    std::vector<int> order(n_envs);
-    std::iota(order.begin(), order.end(), 0);
+    // environments that fit one CTA go to the resident kernel (largest first,
+    // so that its queue balances uneven batches); the others to the tiled path
+    const bool force_tiled = (p->flags & CROWD_FLAG_FORCE_TILED) != 0;
+    std::vector<int> order, tiled;
+    for (int e = 0; e < n_envs; ++e) {
+        if (!force_tiled && agents_per_env[e] <= kResidentMaxAgents) order.push_back(e);
+        else tiled.push_back(e);
+    }
     std::stable_sort(order.begin(), order.end(),
                      [&](int a, int b) { return agents_per_env[a] > agents_per_env[b]; });
+    for (int e : order) h->res_max_agents = std::max(h->res_max_agents, (int)agents_per_env[e]);
+    h->n_res = (int)order.size();
+    h->n_tiled = (int)tiled.size();
+    std::vector<int> seg_cell_start, seg_cell_ids;
+    int total_cells = 0;
+    for (int e : tiled) {
+        TiledEnv te{};
+        build_tiled_env(e, env_start[e], agents_per_env[e], seg_start[e], segs_per_env ? segs_per_env[e] : 0,
+                        robot[e], init_pos, radii, max_speeds, segments, *p, total_cells, te, seg_cell_start,
+                        seg_cell_ids);
+        total_cells += te.W * te.H + 1;
+        h->tiled_max_agents = std::max(h->tiled_max_agents, te.n);
+        h->tiled_max_tiles = std::max(h->tiled_max_tiles, ((te.W + kTile - 1) / kTile) * ((te.H + kTile - 1) / kTile));
+        h->h_tenvs.push_back(te);
+    }
+    std::vector<SegGrid> seg_grids(std::max(n_envs, 1));
+    int seg_off = total_cells;
+    for (int e : order) {
+        seg_grids[e] = build_seg_grid(env_start[e], agents_per_env[e], seg_start[e], segs_per_env ? segs_per_env[e] : 0,
+                                      radii, max_speeds, segments, *p, seg_off, seg_cell_start, seg_cell_ids);
+        seg_off += seg_grids[e].W * seg_grids[e].H + 1;
+    }
+    if (seg_cell_ids.empty()) seg_cell_ids.push_back(0);
+    if (seg_cell_start.empty()) seg_cell_start.push_back(0);
     std::vector<float4> par((size_t)N), state((size_t)N);
     std::vector<float2> goal((size_t)N);
     for (int64_t i = 0; i < N; ++i) {
@@ -234,6 +530,20 @@ crowd_status crowd_create(int32_t n_envs, const int32_t* agents_per_env, const f
     if ((e = dev_alloc(&h->ptr, (size_t)(n))) != cudaSuccess) {    \
         cuda_fail(e, "cudaMalloc " #ptr);                          \
         return bail(e == cudaErrorMemoryAllocation ? CROWD_ENOMEM : CROWD_ECUDA); \
+    }
+    ALLOC(seg_grid, n_envs);
+    ALLOC(seg_cell_start, seg_cell_start.size());
+    ALLOC(seg_cell_ids, seg_cell_ids.size());
+    if (h->n_tiled) {
+        ALLOC(tenvs, h->n_tiled);
+        ALLOC(state_b, N);
+        ALLOC(sorted_pv, N);
+        ALLOC(key, N);
+        ALLOC(rank, N);
+        ALLOC(sorted_id, N);
+        ALLOC(count, total_cells);
+        ALLOC(start, total_cells);
+        ALLOC(d_step, 1);
     }
     ALLOC(env_start, n_envs + 1);
     ALLOC(seg_start, n_envs + 1);
@@ -259,7 +569,11 @@ crowd_status crowd_create(int32_t n_envs, const int32_t* agents_per_env, const f
         {h->env_start, env_start.data(), sizeof(int) * (n_envs + 1)},
         {h->seg_start, seg_start.data(), sizeof(int) * (n_envs + 1)},
         {h->robot_index, robot.data(), sizeof(int) * n_envs},
-        {h->order, order.data(), sizeof(int) * n_envs},
+        {h->order, order.data(), sizeof(int) * order.size()},
+        {h->tenvs, h->h_tenvs.data(), sizeof(TiledEnv) * h->h_tenvs.size()},
+        {h->seg_cell_start, seg_cell_start.data(), sizeof(int) * seg_cell_start.size()},
+        {h->seg_cell_ids, seg_cell_ids.data(), sizeof(int) * seg_cell_ids.size()},
+        {h->seg_grid, seg_grids.data(), sizeof(SegGrid) * n_envs},
         {h->state, state.data(), sizeof(float4) * N},
         {h->par, par.data(), sizeof(float4) * N},
         {h->goal, goal.data(), sizeof(float2) * N},
@@ -278,6 +592,18 @@ crowd_status crowd_create(int32_t n_envs, const int32_t* agents_per_env, const f
         cuda_fail(e, "initialise buffers");
         return bail(CROWD_ECUDA);
     }
+    if (h->count && (e = cudaMemsetAsync(h->count, 0, sizeof(int) * total_cells, h->stream)) != cudaSuccess) {
+        cuda_fail(e, "initialise cell counts");
+        return bail(CROWD_ECUDA);
+    }
+    if (h->n_tiled && (e = tiled_init(kHaloCap)) != cudaSuccess) {
+        cuda_fail(e, "tiled kernel attributes");
+        return bail(CROWD_ECUDA);
+    }
+    if (h->n_tiled && (e = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking)) != cudaSuccess) {
+        cuda_fail(e, "create capture stream");
+        return bail(CROWD_ECUDA);
+    }
     if (h->work && (e = cudaMemsetAsync(h->work, 0, sizeof(WorkCount), h->stream)) != cudaSuccess) {
         cuda_fail(e, "initialise work counters");
         return bail(CROWD_ECUDA);
@@ -290,14 +616,15 @@ crowd_status crowd_create(int32_t n_envs, const int32_t* agents_per_env, const f
     }
 
     // launch shape: one CTA per environment, as many resident per SM as fit
-    h->block = resident_block_threads(max_agents);
+    h->block = resident_block_threads(h->res_max_agents);
+    h->halo_cap = kHaloCap;
     int sms = 0;
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device)) != cudaSuccess) {
         cuda_fail(e, "device attributes");
         return bail(CROWD_ECUDA);
     }
-    const int per_sm = std::max(1, resident_ctas_per_sm(max_agents, h->block, p->max_neighbors));
-    h->grid = std::max(1, std::min(n_envs, per_sm * sms));
+    const int per_sm = std::max(1, resident_ctas_per_sm(h->res_max_agents, h->block, p->max_neighbors));
+    h->grid = std::max(1, std::min(std::max(h->n_res, 1), per_sm * sms));
 
     if ((e = cudaStreamSynchronize(h->stream)) != cudaSuccess) {
         cuda_fail(e, "synchronize after create");
@@ -352,39 +679,49 @@ crowd_status crowd_step(crowd_t h, float dt, const float* robot_vel, int32_t ptr
             rv = (const float2*)robot_vel;
         }
     }
-    ResidentArgs a{};
-    a.n_work = h->E;
-    a.order = h->order;
-    a.queue = h->queue;
-    a.env_start = h->env_start;
-    a.seg_start = h->seg_start;
-    a.robot_index = h->robot_index;
-    a.segs = h->segs;
-    a.par = h->par;
-    a.goal = h->goal;
-    a.state = h->state;
-    a.robot_vel = rv;
-    a.robot_stride = h->E;
-    a.n_steps = n_steps;
-    a.dt = dt;
-    a.tau = h->p.time_horizon;
-    a.tau_o = h->p.time_horizon_obst > 0.f ? h->p.time_horizon_obst : h->p.time_horizon;
-    a.R = h->p.neighbor_dist;
-    a.robot_alpha = h->p.robot_responsibility;
-    a.K = h->p.max_neighbors;
-    a.nbr_out = h->nbr;
     const bool stats = (h->p.flags & CROWD_FLAG_STATS) != 0;
-    a.stats = stats ? h->stats : nullptr;
-    a.reach = stats ? h->reach : nullptr;
-    a.step_base = h->step_index;
-    a.work = h->work;
-    a.err = h->err;
-    a.max_agents = h->max_agents;
-    CUDA_TRY(cudaMemsetAsync(h->queue, 0, sizeof(int), h->stream), "reset work queue");
-    cudaError_t e = launch_resident(a, h->grid, h->block, h->stream);
-    if (e != cudaSuccess) {
-        h->broken = e != cudaErrorInvalidValue && e != cudaErrorInvalidConfiguration;
-        return cuda_fail(e, "launch crowd step");
+    const float tau_o = h->p.time_horizon_obst > 0.f ? h->p.time_horizon_obst : h->p.time_horizon;
+    if (h->n_res) {
+        ResidentArgs a{};
+        a.n_work = h->n_res;
+        a.order = h->order;
+        a.queue = h->queue;
+        a.env_start = h->env_start;
+        a.seg_start = h->seg_start;
+        a.robot_index = h->robot_index;
+        a.segs = h->segs;
+        a.seg_grid = h->seg_grid;
+        a.seg_cell_start = h->seg_cell_start;
+        a.seg_cell_ids = h->seg_cell_ids;
+        a.par = h->par;
+        a.goal = h->goal;
+        a.state = h->state;
+        a.robot_vel = rv;
+        a.robot_stride = h->E;
+        a.n_steps = n_steps;
+        a.dt = dt;
+        a.tau = h->p.time_horizon;
+        a.tau_o = tau_o;
+        a.R = h->p.neighbor_dist;
+        a.robot_alpha = h->p.robot_responsibility;
+        a.K = h->p.max_neighbors;
+        a.nbr_out = h->nbr;
+        a.stats = stats ? h->stats : nullptr;
+        a.reach = stats ? h->reach : nullptr;
+        a.step_base = h->step_index;
+        a.work = h->work;
+        a.err = h->err;
+        a.max_agents = h->res_max_agents;
+        CUDA_TRY(cudaMemsetAsync(h->queue, 0, sizeof(int), h->stream), "reset work queue");
+        cudaError_t e = launch_resident(a, h->grid, h->block, h->stream);
+        if (e != cudaSuccess) {
+            h->broken = e != cudaErrorInvalidValue && e != cudaErrorInvalidConfiguration;
+            return cuda_fail(e, "launch crowd step");
+        }
+    }
+    if (h->n_tiled) {
+        st = tiled_steps(h, dt, rv, n_steps, stats, tau_o);
+        if (st) return st;
     }
     h->step_index += n_steps;
     return CROWD_OK;

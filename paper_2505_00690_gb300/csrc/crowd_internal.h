@@ -38,6 +38,17 @@ struct WorkCount {
         lp_solve_lines, fallbacks;
 };
 
+// Static grid over an environment's segments with, per cell, the ascending
+// list of segments that can come within reach (r + tau_obst v_max, maximised
+// over the environment's agents) of a point of the cell; agents outside the
+// grid use the nearest border cell.  Lists of cell k of the environment are
+// seg_cell_ids[seg_cell_start[off + k] .. seg_cell_start[off + k + 1]).
+struct SegGrid {
+    float x0, y0, inv_c;
+    int W, H;
+    int off;
+};
+
 // Arguments of one launch of the resident kernel: every listed environment
 // is advanced n_steps steps, reading and writing `state` in place.
 struct ResidentArgs {
@@ -48,6 +59,9 @@ struct ResidentArgs {
     const int* seg_start;   // [E+1]
     const int* robot_index; // [E] env-local or -1
     const float4* segs;     // [S] (ax, ay, bx, by)
+    const SegGrid* seg_grid;      // [E]
+    const int* seg_cell_start;    // per-cell segment lists (see SegGrid)
+    const int* seg_cell_ids;
     const float4* par;      // [N] (radius, v_max, preferred speed, 0)
     const float2* goal;     // [N]
     float4* state;          // [N] (px, py, vx, vy)
@@ -65,7 +79,66 @@ struct ResidentArgs {
     int max_agents;         // largest environment in `order` (sizes shared memory)
 };
 
-size_t resident_smem_bytes(int max_agents);
+// One large environment of the tiled path (static uniform grid, cell >= R).
+struct TiledEnv {
+    int e;          // environment id
+    int base, n;    // agents [base, base + n)
+    int seg0;       // first segment of the environment
+    int robot;      // environment-local robot index or -1
+    int co;         // offset of the environment's cells in count/start/segment-list arrays
+    int W, H;       // grid cells
+    float x0, y0, inv_c;
+};
+
+// Cells per side of a tile of the tiled update kernel.
+constexpr int kTile = 4;
+// Largest grid side of a tiled environment.
+constexpr int kTiledGridMax = 512;
+
+enum : int { kTiledStep = 0, kTiledStepCount = 1, kTiledStatsOnly = 2 };
+
+// Arguments of one step of the tiled path.
+struct TiledStepArgs {
+    const TiledEnv* envs;
+    int n_envs;
+    float4* state_in;         // [N] state at the start of the step (robot slots get their command)
+    float4* state_out;        // [N] state after the step
+    const float2* robot_vel;  // [E] commands of this step, or null (keep current)
+    const float4* par;
+    const float2* goal;
+    const float4* segs;
+    const int* seg_cell_start;  // [cells + 1 per env] per-cell segment lists
+    const int* seg_cell_ids;
+    int* key;                 // [N] scratch: cell of each agent
+    int* rank;                // [N] scratch: rank inside the cell
+    int* count;               // [cells] scratch: zero between steps
+    int* start;               // [cells + 1 per env] scratch: cell starts (global sorted slots)
+    float4* sorted_pv;        // [N] scratch: state in cell order
+    int* sorted_id;           // [N] scratch: environment-local index of each sorted slot
+    int halo_cap;             // agents the update kernel stages in shared memory
+    float R, dt, tau, tau_o, robot_alpha;
+    int K;
+    int mode;                 // kTiledStep / kTiledStepCount / kTiledStatsOnly
+    int* nbr_out;             // [N][K] or null
+    EnvStats* stats;          // [E] or null
+    int* reach;               // [N] (with stats)
+    long long* step_index;    // device step counter (reach steps are 1-based from it)
+    WorkCount* work;
+    int* err;
+};
+
+// Halo agents the tiled update kernel stages in shared memory (60 KB).
+constexpr int kHaloCap = 3072;
+
+size_t tiled_smem_bytes(int halo_cap);
+// One-time kernel attributes of the tiled path (before any capture).
+cudaError_t tiled_init(int halo_cap);
+// Enqueue one thread setting the device step counter.
+cudaError_t launch_set_step(long long* p, long long value, cudaStream_t s);
+// Enqueue one step of the tiled path (4 kernels + bookkeeping).
+cudaError_t launch_tiled_step(const TiledStepArgs& a, int max_agents, int max_tiles, cudaStream_t s);
+
+size_t resident_smem_bytes(int max_agents, int K, int block);
 int resident_block_threads(int max_agents);
 int resident_kmax(int K);
 // Launch on `stream`; `grid` CTAs pull environments from the queue.

@@ -28,6 +28,7 @@
 #include <stdint.h>
 
 #include "crowd_internal.h"
+#include "crowd_agent.cuh"
 #include "orca_device.cuh"
 
 namespace crowd {
@@ -47,12 +48,25 @@ struct Smem {
     int* cell;     // [kMaxCells + 1] counts, then starts
     unsigned short* key;   // [Nm] cell of each agent
     unsigned short* rank;  // [Nm] rank of each agent inside its cell
+    FbEntry* fb;           // [fb_cap] agents queued for the cooperative fallback
+    Line* fb_lines;        // [fb_cap][lmax] their lines
+    Line* fb_scratch;      // [warps][lmax] subproblem lines of each warp
+    int fb_cap, lmax;
 };
+
+// Fallback queue capacity: about 1/16 of the agents, 8..32 (the urban block
+// has ~2.5% infeasible LPs per step; overflow falls back per thread).
+__host__ __device__ inline int fb_capacity(int max_agents) {
+    const int c = (max_agents + 15) / 16;
+    return c < 8 ? 8 : (c > 32 ? 32 : c);
+}
 
 __host__ __device__ inline int round_up4(int n) { return (n + 3) & ~3; }
 
-__host__ __device__ inline size_t smem_layout(int max_agents, Smem* s, unsigned char* base) {
+__host__ __device__ inline size_t smem_layout(int max_agents, int kmax, int warps, Smem* s, unsigned char* base) {
     const int nm = round_up4(max_agents > 0 ? max_agents : 1);
+    const int lmax = kmax + kMaxObstacleLines;
+    const int fb_cap = fb_capacity(max_agents);
     size_t off = 0;
     auto take = [&](size_t bytes) {
         unsigned char* p = base ? base + off : nullptr;
@@ -68,6 +82,9 @@ __host__ __device__ inline size_t smem_layout(int max_agents, Smem* s, unsigned 
     unsigned char* cell = take(sizeof(int) * (kMaxCells + 1));
     unsigned char* key = take(sizeof(unsigned short) * nm);
     unsigned char* rank = take(sizeof(unsigned short) * nm);
+    unsigned char* fb = take(sizeof(FbEntry) * fb_cap);
+    unsigned char* fb_lines = take(sizeof(Line) * fb_cap * lmax);
+    unsigned char* fb_scratch = take(sizeof(Line) * warps * lmax);
     if (s) {
         s->pv = (float4*)pv;
         s->nv = (float4*)nv;
@@ -78,6 +95,11 @@ __host__ __device__ inline size_t smem_layout(int max_agents, Smem* s, unsigned 
         s->cell = (int*)cell;
         s->key = (unsigned short*)key;
         s->rank = (unsigned short*)rank;
+        s->fb = (FbEntry*)fb;
+        s->fb_lines = (Line*)fb_lines;
+        s->fb_scratch = (Line*)fb_scratch;
+        s->fb_cap = fb_cap;
+        s->lmax = lmax;
     }
     return off;
 }
@@ -180,185 +202,45 @@ __device__ __forceinline__ void sort_by_cell(const Smem& S, int n, const Grid& g
     __syncthreads();
 }
 
-// Distance from p to the bounding box of a segment, squared (a cheap lower
-// bound of the segment distance used to skip far segments).
-__device__ __forceinline__ float box_dist2(float px, float py, float4 s) {
-    const float dx = fmaxf(fmaxf(fminf(s.x, s.z) - px, px - fmaxf(s.x, s.z)), 0.f);
-    const float dy = fmaxf(fmaxf(fminf(s.y, s.w) - py, py - fmaxf(s.y, s.w)), 0.f);
-    return dx * dx + dy * dy;
-}
-
-// Per-thread work tallies (only kept when counting is on).
-struct Tally {
-    unsigned long long agent_steps = 0, candidates = 0, agent_lines = 0, obstacle_lines = 0, segment_tests = 0,
-                       lp_checks = 0, lp_solves = 0, lp_solve_lines = 0, fallbacks = 0;
-};
-
 struct StepCtx {
     int e, base, n, robot, seg0, ns;
-    int step;        // 0-based step inside this launch
-    bool last;       // last step of the launch
+    SegGrid sg;
+    int step;  // 0-based step inside this launch
+    bool last;  // last step of the launch
     Grid g;
 };
 
-template <int KMAX>
-struct NbList {
-    int id[KMAX];
-    int cnt;
+// Candidates of the environment in cell order, in shared memory.
+struct SmemSource {
+    const float4* spv;
+    const int* sid;
+    const int* cell;
+    int W;
+    __device__ __forceinline__ int2 row(int yy, int xa, int xb) const {
+        return make_int2(cell[yy * W + xa], cell[yy * W + xb + 1]);
+    }
+    __device__ __forceinline__ float4 cand(int u) const { return spv[u]; }
+    __device__ __forceinline__ int cand_id(int u) const { return sid[u]; }
 };
 
-// K nearest agents within R of the agent in sorted slot t, ordered by
-// (FP64 key, index) exactly as the definition ranks them.  Candidates are
-// ranked by their FP32 squared distance (packed with the index into one
-// 64-bit key); FP32 and FP64 keys further apart than kKeyRelErr order alike,
-// so the FP32 order is exact unless two of the first K+1 keys are closer than
-// that, in which case the block is rescanned with FP64 keys.  Candidates
-// within kKeyRelErr of R^2 are admitted by their FP64 key.
-template <int KMAX>
-__device__ __forceinline__ void select_neighbors(const Smem& S, const StepCtx& c, int t, float4 me, float R, int K,
-                                                 NbList<KMAX>& out, Tally& w) {
-    const float R2 = R * R;
-    const float R2hi = R2 * (1.f + kKeyRelErr), R2lo = R2 * (1.f - kKeyRelErr);
-    const double Rd = (double)R;
-    const unsigned long long R2bits = (unsigned long long)__double_as_longlong(__dmul_rn(Rd, Rd));
-    const double xi = (double)me.x, yi = (double)me.y;
-    const int cx = cell_coord(me.x, c.g.x0, c.g.inv_c, c.g.W);
-    const int cy = cell_coord(me.y, c.g.y0, c.g.inv_c, c.g.H);
-    const int xa = max(cx - 1, 0), xb = min(cx + 1, c.g.W - 1);
-    const int ya = max(cy - 1, 0), yb = min(cy + 1, c.g.H - 1);
-    TopK32<KMAX + 1> top;
-    top.init();
-    for (int yy = ya; yy <= yb; ++yy) {
-        const int b0 = S.cell[yy * c.g.W + xa], b1 = S.cell[yy * c.g.W + xb + 1];
-        w.candidates += (unsigned long long)(b1 - b0);
-        for (int u = b0; u < b1; ++u) {
-            const float4 o = S.spv[u];
-            const float dx = o.x - me.x, dy = o.y - me.y;
-            const float d2 = dx * dx + dy * dy;
-            if (d2 < R2hi && u != t) {
-                if (d2 > R2lo && !(rank_key(xi, yi, o.x, o.y) < R2bits)) continue;
-                top.insert(((unsigned long long)__float_as_uint(d2) << 32) | (unsigned)S.sid[u], K + 1);
-            }
-        }
-    }
-    bool near_tie = false;
-#pragma unroll
-    for (int s = 0; s < KMAX; ++s) {
-        if (s < K && s + 1 < top.cnt) {
-            const float ka = TopK32<KMAX + 1>::key_of(top.e[s]), kb = TopK32<KMAX + 1>::key_of(top.e[s + 1]);
-            if (kb - ka <= kKeyRelErr * kb) near_tie = true;
-        }
-    }
-    if (!near_tie) {
-        out.cnt = min(top.cnt, K);
-#pragma unroll
-        for (int s = 0; s < KMAX; ++s) out.id[s] = (int)(unsigned)(top.e[s] & 0xffffffffull);
-        return;
-    }
-    TopK64<KMAX> nb;
-    nb.init();
-    for (int yy = ya; yy <= yb; ++yy) {
-        const int b0 = S.cell[yy * c.g.W + xa], b1 = S.cell[yy * c.g.W + xb + 1];
-        for (int u = b0; u < b1; ++u) {
-            if (u == t) continue;
-            const float4 o = S.spv[u];
-            const unsigned long long k = rank_key(xi, yi, o.x, o.y);
-            if (k < R2bits) nb.insert(k, S.sid[u], K);
-        }
-    }
-    out.cnt = nb.cnt;
-#pragma unroll
-    for (int s = 0; s < KMAX; ++s) out.id[s] = nb.id[s];
+// Agents of the environment by index, in shared memory.
+struct SmemAgents {
+    const float4* pv;
+    const float4* par;
+    __device__ __forceinline__ float4 state(int j) const { return pv[j]; }
+    __device__ __forceinline__ float radius(int j) const { return par[j].x; }
+};
+
+// The segment list of the static segment-grid cell holding position `me`.
+__device__ __forceinline__ ListedSegments cell_segments(const ResidentArgs& a, const StepCtx& c, float4 me) {
+    const int k = cell_coord(me.y, c.sg.y0, c.sg.inv_c, c.sg.H) * c.sg.W + cell_coord(me.x, c.sg.x0, c.sg.inv_c, c.sg.W);
+    const int s0 = __ldg(&a.seg_cell_start[c.sg.off + k]), s1 = __ldg(&a.seg_cell_start[c.sg.off + k + 1]);
+    return ListedSegments{a.seg_cell_ids + s0, s1 - s0};
 }
 
-template <int KMAX>
-__device__ __forceinline__ void agent_update(const ResidentArgs& a, const Smem& S, const StepCtx& c, int t,
-                                             double& speed_acc, Tally& w) {
-    const int i = S.sid[t];
-    const float4 me = S.spv[t];
-    const float4 pr = S.par[i];
-
-    // ---- A1/A2: K nearest within R, ranked by (FP64 key, index)
-    NbList<KMAX> nb;
-    select_neighbors<KMAX>(S, c, t, me, a.R, a.K, nb, w);
-    const int K = a.K;
-    if (c.last && a.nbr_out) {
-        int* out = a.nbr_out + (size_t)(c.base + i) * K;
-#pragma unroll
-        for (int s = 0; s < KMAX; ++s)
-            if (s < K) out[s] = s < nb.cnt ? nb.id[s] : -1;
-    }
-
-    float2 v;
-    if (i == c.robot) {
-        v = make_float2(me.z, me.w);  // commanded, not solved
-    } else {
-        const float2 gl = S.goal[i];
-        const float2 pref = pref_velocity(me.x, me.y, gl.x, gl.y, pr.z, a.dt);
-        Line L[KMAX + kMaxObstacleLines];
-
-        // ---- A4: segments within r + tau_o v_max, ordered by (distance^2, id)
-        const float reach = pr.x + a.tau_o * pr.y;
-        const float reach2 = reach * reach;
-        float okey[kMaxObstacleLines];
-        int oid[kMaxObstacleLines];
-        int no = 0;
-        for (int s = 0; s < c.ns; ++s) {
-            const float4 sg = __ldg(&a.segs[c.seg0 + s]);
-            if (box_dist2(me.x, me.y, sg) >= reach2) continue;
-            ++w.segment_tests;
-            float qx, qy;
-            const float d2 = seg_dist2(me.x, me.y, sg, qx, qy);
-            if (!(d2 < reach2)) continue;
-            if (no == kMaxObstacleLines) {
-                atomicOr(a.err, kErrObstacleOverflow);
-                if (!(d2 < okey[no - 1])) continue;
-                --no;  // drop the farthest
-            }
-            int p = no;
-            while (p > 0 && okey[p - 1] > d2) {
-                okey[p] = okey[p - 1];
-                oid[p] = oid[p - 1];
-                --p;
-            }
-            okey[p] = d2;
-            oid[p] = s;
-            ++no;
-        }
-        for (int k = 0; k < no; ++k)
-            L[k] = obstacle_line(me.x, me.y, me.z, me.w, pr.x, pr.y, __ldg(&a.segs[c.seg0 + oid[k]]), a.tau_o,
-                                 a.dt);
-
-        // ---- A3: one reciprocal half-plane per neighbour, in list order
-#pragma unroll
-        for (int s = 0; s < KMAX; ++s) {
-            if (s < nb.cnt) {
-                const int j = nb.id[s];
-                const float4 o = S.pv[j];
-                const float alpha = (j == c.robot) ? a.robot_alpha : 0.5f;
-                L[no + s] = agent_line(me.x, me.y, me.z, me.w, pr.x, o.x, o.y, o.z, o.w, S.par[j].x, a.tau, a.dt,
-                                       alpha, i < j);
-            }
-        }
-
-        // ---- A5: LP, fallback when infeasible
-        const int nl = no + nb.cnt;
-        int solves = 0, solve_lines = 0;
-        const bool feasible = lp2(L, nl, pr.y, pref, v, solves, solve_lines) == nl;
-        if (!feasible) {
-            Line scratch[KMAX + kMaxObstacleLines];
-            v = lp_fallback(L, nl, no, pr.y, pref, scratch);
-        }
-        w.agent_lines += nb.cnt;
-        w.obstacle_lines += no;
-        w.lp_checks += nl;
-        w.lp_solves += solves;
-        w.lp_solve_lines += solve_lines;
-        w.fallbacks += feasible ? 0 : 1;
-    }
-    ++w.agent_steps;
-
-    // ---- A6: integrate into the next-state buffer
+// A6 for agent i: integrate into the next-state buffer, statistics.
+__device__ __forceinline__ void integrate(const ResidentArgs& a, const Smem& S, const StepCtx& c, int i, float4 me,
+                                          float r, float2 v, double& speed_acc) {
     float4 nx;
     nx.x = fmaf(a.dt, v.x, me.x);
     nx.y = fmaf(a.dt, v.y, me.y);
@@ -371,8 +253,55 @@ __device__ __forceinline__ void agent_update(const ResidentArgs& a, const Smem& 
             int* rp = a.reach + c.base + i;
             const float2 gl = S.goal[i];
             const float gx = gl.x - nx.x, gy = gl.y - nx.y;
-            if (*rp < 0 && sqrtf(gx * gx + gy * gy) <= pr.x) *rp = (int)(a.step_base + c.step + 1);
+            if (*rp < 0 && sqrtf(gx * gx + gy * gy) <= r) *rp = (int)(a.step_base + c.step + 1);
         }
+    }
+}
+
+template <int KMAX>
+__device__ __forceinline__ void agent_update(const ResidentArgs& a, const AgentParams& ap, const Smem& S,
+                                             const StepCtx& c, int t, double& speed_acc, Tally& w,
+                                             const FbQueue& fbq) {
+    const int i = S.sid[t];
+    const float4 me = S.spv[t];
+    const float4 pr = S.par[i];
+
+    // A1/A2: K nearest within R, ranked by (FP64 key, index)
+    NbList<KMAX> nb;
+    const SmemSource src{S.spv, S.sid, S.cell, c.g.W};
+    select_neighbors<KMAX>(src, cell_coord(me.x, c.g.x0, c.g.inv_c, c.g.W),
+                           cell_coord(me.y, c.g.y0, c.g.inv_c, c.g.H), c.g.W, c.g.H, i, me, a.R, a.K, nb, w);
+    const int K = a.K;
+    if (c.last && a.nbr_out) {
+        int* out = a.nbr_out + (size_t)(c.base + i) * K;
+#pragma unroll
+        for (int s = 0; s < KMAX; ++s)
+            if (s < K) out[s] = s < nb.cnt ? nb.id[s] : -1;
+    }
+
+    // A3-A5 (the robot is not solved: it keeps its command); an infeasible
+    // LP is queued for the warp-cooperative fallback, integrated there
+    ++w.agent_steps;
+    if (i == c.robot) {
+        integrate(a, S, c, i, me, pr.x, make_float2(me.z, me.w), speed_acc);
+        return;
+    }
+    bool queued;
+    const float2 v = solve_velocity<KMAX>(ap, SmemAgents{S.pv, S.par}, i, c.robot, me, pr, S.goal[i], c.seg0,
+                                          cell_segments(a, c, me), nb, w, &fbq, queued);
+    if (!queued) integrate(a, S, c, i, me, pr.x, v, speed_acc);
+}
+
+// The queued fallbacks of this step, one warp per agent.
+__device__ __forceinline__ void run_fallbacks(const ResidentArgs& a, const Smem& S, const StepCtx& c, int n_queued,
+                                              double& speed_acc) {
+    const int warp = threadIdx.x >> 5, warps = blockDim.x >> 5;
+    Line* scratch = S.fb_scratch + (size_t)warp * S.lmax;
+    for (int q = warp; q < n_queued; q += warps) {
+        const FbEntry f = S.fb[q];
+        const float2 v = coop_fallback(S.fb_lines + (size_t)q * S.lmax, f.n, f.n_hard, f.vmax, f.pref, scratch);
+        if ((threadIdx.x & 31) == 0) integrate(a, S, c, f.agent, f.me, S.par[f.agent].x, v, speed_acc);
+        __syncwarp();
     }
 }
 
@@ -398,8 +327,9 @@ __device__ __forceinline__ void count_collisions(const ResidentArgs& a, const Sm
         }
     }
     const float lim = ri - kCollideDepth;
-    for (int s = 0; s < c.ns; ++s) {
-        const float4 sg = __ldg(&a.segs[c.seg0 + s]);
+    const ListedSegments sl = cell_segments(a, c, me);
+    for (int q = 0; q < sl.count(); ++q) {
+        const float4 sg = __ldg(&a.segs[c.seg0 + sl.id(q)]);
         if (box_dist2(me.x, me.y, sg) >= lim * lim) continue;
         float qx, qy;
         if (sqrtf(seg_dist2(me.x, me.y, sg, qx, qy)) < lim) ++cs;
@@ -415,7 +345,8 @@ __global__ void __launch_bounds__(kMaxThreads) resident_kernel(ResidentArgs a) {
     __shared__ unsigned long long s_ca, s_cs;
     __shared__ double s_speed;
     Smem S;
-    smem_layout(a.max_agents, &S, smem_raw);
+    smem_layout(a.max_agents, KMAX, blockDim.x >> 5, &S, smem_raw);
+    __shared__ int s_fb_count;
 
     for (;;) {
         if (threadIdx.x == 0) s_work = atomicAdd(a.queue, 1);
@@ -429,6 +360,7 @@ __global__ void __launch_bounds__(kMaxThreads) resident_kernel(ResidentArgs a) {
         c.robot = a.robot_index[c.e];
         c.seg0 = a.seg_start[c.e];
         c.ns = a.seg_start[c.e + 1] - c.seg0;
+        c.sg = a.seg_grid[c.e];
         for (int i = threadIdx.x; i < c.n; i += blockDim.x) {
             S.pv[i] = a.state[c.base + i];
             S.par[i] = __ldg(&a.par[c.base + i]);
@@ -444,6 +376,8 @@ __global__ void __launch_bounds__(kMaxThreads) resident_kernel(ResidentArgs a) {
         double speed_acc = 0.0;
         unsigned long long ca = 0, cs = 0;
         Tally tally;
+        const AgentParams ap{a.R, a.dt, a.tau, a.tau_o, a.robot_alpha, a.K, a.segs, a.err};
+        const FbQueue fbq{&s_fb_count, S.fb_cap, S.lmax, S.fb, S.fb_lines};
         const int passes = a.n_steps + (a.stats ? 1 : 0);
         for (int step = 0; step < passes; ++step) {
             const bool compute = step < a.n_steps;
@@ -461,27 +395,23 @@ __global__ void __launch_bounds__(kMaxThreads) resident_kernel(ResidentArgs a) {
             if (a.stats && step > 0)
                 for (int t = threadIdx.x; t < c.n; t += blockDim.x) count_collisions(a, S, c, t, ca, cs);
             if (!compute) break;
-            for (int t = threadIdx.x; t < c.n; t += blockDim.x) agent_update<KMAX>(a, S, c, t, speed_acc, tally);
+            if (threadIdx.x == 0) s_fb_count = 0;
             __syncthreads();
+            for (int t = threadIdx.x; t < c.n; t += blockDim.x)
+                agent_update<KMAX>(a, ap, S, c, t, speed_acc, tally, fbq);
+            __syncthreads();
+            const int n_queued = min(s_fb_count, S.fb_cap);
+            if (n_queued) {
+                run_fallbacks(a, S, c, n_queued, speed_acc);
+                __syncthreads();
+            }
             float4* tmp = S.pv;
             S.pv = S.nv;
             S.nv = tmp;
         }
         __syncthreads();
         for (int i = threadIdx.x; i < c.n; i += blockDim.x) a.state[c.base + i] = S.pv[i];
-        if (a.work) {
-            unsigned long long* dst = &a.work->agent_steps;
-            const unsigned long long vals[9] = {tally.agent_steps, tally.candidates, tally.agent_lines,
-                                                tally.obstacle_lines, tally.segment_tests, tally.lp_checks,
-                                                tally.lp_solves, tally.lp_solve_lines, tally.fallbacks};
-#pragma unroll
-            for (int q = 0; q < 9; ++q) {
-                unsigned long long v = vals[q];
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-                if ((threadIdx.x & 31) == 0 && v) atomicAdd(dst + q, v);
-            }
-        }
+        if (a.work) flush_tally(tally, a.work);
         if (a.stats) {
             if (ca) atomicAdd(&s_ca, ca);
             if (cs) atomicAdd(&s_cs, cs);
@@ -501,7 +431,7 @@ __global__ void __launch_bounds__(kMaxThreads) resident_kernel(ResidentArgs a) {
 
 template <int KMAX>
 cudaError_t launch_k(const ResidentArgs& a, int grid, int block, cudaStream_t stream) {
-    const size_t smem = resident_smem_bytes(a.max_agents);
+    const size_t smem = smem_layout(a.max_agents, KMAX, block / 32, nullptr, nullptr);
     cudaError_t err = cudaFuncSetAttribute(resident_kernel<KMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            (int)smem);
     if (err != cudaSuccess) return err;
@@ -511,7 +441,7 @@ cudaError_t launch_k(const ResidentArgs& a, int grid, int block, cudaStream_t st
 
 template <int KMAX>
 int ctas_k(int max_agents, int block) {
-    const size_t smem = resident_smem_bytes(max_agents);
+    const size_t smem = smem_layout(max_agents, KMAX, block / 32, nullptr, nullptr);
     if (cudaFuncSetAttribute(resident_kernel<KMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
         cudaSuccess)
         return 0;
@@ -522,7 +452,9 @@ int ctas_k(int max_agents, int block) {
 
 }  // namespace
 
-size_t resident_smem_bytes(int max_agents) { return smem_layout(max_agents, nullptr, nullptr); }
+size_t resident_smem_bytes(int max_agents, int K, int block) {
+    return smem_layout(max_agents, resident_kmax(K), block / 32, nullptr, nullptr);
+}
 
 int resident_block_threads(int max_agents) {
     int b = ((max_agents + 31) / 32) * 32;

@@ -1,0 +1,369 @@
+// Tiled crowd step for environments too large to live in one CTA.
+//
+// The paper's simulator advances every dynamic agent of every environment
+// each step (Sec. 3.2); a city-scale scene (Appendix "Data") holds far more
+// agents than one SM's shared memory.  For such environments one step is
+// four kernels over global memory:
+//   tiled_count    robot command, cell key (static per-environment grid with
+//                  cell size >= R) and rank inside the cell (atomic count);
+//   tiled_scan     one CTA per environment turns the counts into cell starts
+//                  (block scan) and clears the counts for the next step;
+//   tiled_scatter  writes the state in cell order;
+//   tiled_update   one CTA per (environment, tile of kTile x kTile cells):
+//                  stages the tile's halo cells (already contiguous in cell
+//                  order) into shared memory, then each thread takes the
+//                  tile's agents: K nearest from the staged halo, segment
+//                  half-planes from the cell's precomputed segment list,
+//                  agent half-planes, LP, integration into the other buffer.
+// Multi-step calls replay these launches from a CUDA graph (captured by the
+// host side).  Agents outside the grid are clamped into the border cells,
+// which keeps the 3x3-cell search exact (clamping onto a box is
+// non-expansive).
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "crowd_agent.cuh"
+#include "crowd_internal.h"
+#include "orca_device.cuh"
+
+namespace crowd {
+
+namespace {
+
+constexpr int kCountThreads = 256;
+constexpr int kScanThreads = 1024;
+constexpr int kUpdateThreads = 256;
+
+__device__ __forceinline__ int clamp_cell(float v, float v0, float inv_c, int n) {
+    const int c = __float2int_rd((v - v0) * inv_c);
+    return min(max(c, 0), n - 1);
+}
+
+__device__ __forceinline__ int cell_of(const TiledEnv& te, float x, float y) {
+    return clamp_cell(y, te.y0, te.inv_c, te.H) * te.W + clamp_cell(x, te.x0, te.inv_c, te.W);
+}
+
+__global__ void __launch_bounds__(kCountThreads) tiled_count(TiledStepArgs a) {
+    const TiledEnv te = a.envs[blockIdx.y];
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= te.n) return;
+    const int g = te.base + i;
+    float4 p = a.state_in[g];
+    if (i == te.robot && a.robot_vel) {
+        const float2 cmd = __ldg(&a.robot_vel[te.e]);
+        p.z = cmd.x;
+        p.w = cmd.y;
+        a.state_in[g] = p;
+    }
+    const int k = cell_of(te, p.x, p.y);
+    a.key[g] = k;
+    a.rank[g] = atomicAdd(&a.count[te.co + k], 1);
+}
+
+// Exclusive scan of one environment's cell counts into global sorted slots;
+// start[co + W*H] closes the last cell.  Counts are cleared for the next step.
+__global__ void __launch_bounds__(kScanThreads) tiled_scan(TiledStepArgs a) {
+    __shared__ int warp_sum[kScanThreads / 32];
+    __shared__ int carry;
+    const TiledEnv te = a.envs[blockIdx.x];
+    const int C = te.W * te.H;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) carry = te.base;
+    __syncthreads();
+    for (int c0 = 0; c0 < C; c0 += blockDim.x) {
+        const int c = c0 + threadIdx.x;
+        const int v = c < C ? a.count[te.co + c] : 0;
+        int incl = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        if (lane == 31) warp_sum[warp] = incl;
+        __syncthreads();
+        if (warp == 0) {
+            const int nw = blockDim.x >> 5;
+            int ws = lane < nw ? warp_sum[lane] : 0;
+            int wincl = ws;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, wincl, o);
+                if (lane >= o) wincl += y;
+            }
+            if (lane < nw) warp_sum[lane] = wincl - ws;  // exclusive warp offsets
+        }
+        __syncthreads();
+        const int base = carry;
+        if (c < C) {
+            a.start[te.co + c] = base + warp_sum[warp] + incl - v;
+            a.count[te.co + c] = 0;
+        }
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1) carry = base + warp_sum[warp] + incl;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) a.start[te.co + C] = carry;
+}
+
+__global__ void __launch_bounds__(kCountThreads) tiled_scatter(TiledStepArgs a) {
+    const TiledEnv te = a.envs[blockIdx.y];
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= te.n) return;
+    const int g = te.base + i;
+    const int slot = a.start[te.co + a.key[g]] + a.rank[g];
+    a.sorted_pv[slot] = a.state_in[g];
+    a.sorted_id[slot] = i;
+}
+
+// Candidates of the tile's halo staged in shared memory.  Global sorted
+// slots of halo row r (cells hx0..hx1) start at row_slot[r] and sit at
+// smem offset row_off[r].
+struct HaloSource {
+    const float4* pv;
+    const int* id;
+    const int* start;  // global cell starts of the environment (start + co)
+    const int* row_slot;
+    const int* row_off;
+    int W, hy0;
+    __device__ __forceinline__ int2 row(int yy, int xa, int xb) const {
+        const int r = yy - hy0;
+        const int d = row_off[r] - row_slot[r];
+        return make_int2(start[yy * W + xa] + d, start[yy * W + xb + 1] + d);
+    }
+    __device__ __forceinline__ float4 cand(int u) const { return pv[u]; }
+    __device__ __forceinline__ int cand_id(int u) const { return id[u]; }
+};
+
+// Candidates read straight from the global sorted arrays (halo too large).
+struct GlobalSource {
+    const float4* pv;
+    const int* id;
+    const int* start;
+    int W;
+    __device__ __forceinline__ int2 row(int yy, int xa, int xb) const {
+        return make_int2(start[yy * W + xa], start[yy * W + xb + 1]);
+    }
+    __device__ __forceinline__ float4 cand(int u) const { return pv[u]; }
+    __device__ __forceinline__ int cand_id(int u) const { return id[u]; }
+};
+
+// Neighbour states by environment-local index from the step's input buffer.
+struct GlobalAgents {
+    const float4* pv;
+    const float4* par;
+    __device__ __forceinline__ float4 state(int j) const { return pv[j]; }
+    __device__ __forceinline__ float radius(int j) const { return __ldg(&par[j]).x; }
+};
+
+template <int KMAX, class Src>
+__device__ __forceinline__ void tile_agent(const TiledStepArgs& a, const AgentParams& ap, const TiledEnv& te,
+                                           const Src& src, int slot, Tally& w, unsigned long long& ca,
+                                           unsigned long long& cs, double& speed) {
+    const int i = a.sorted_id[slot];
+    const float4 me = a.sorted_pv[slot];
+    const int g = te.base + i;
+    const float4 pr = __ldg(&a.par[g]);
+    const int k = cell_of(te, me.x, me.y);
+    const int cx = k % te.W, cy = k / te.W;
+
+    if (a.mode != kTiledStep) {
+        // collision events of the input state (the previous step's result)
+        const int xa = max(cx - 1, 0), xb = min(cx + 1, te.W - 1);
+        for (int yy = max(cy - 1, 0); yy <= min(cy + 1, te.H - 1); ++yy) {
+            const int2 r = src.row(yy, xa, xb);
+            for (int u = r.x; u < r.y; ++u) {
+                const int j = src.cand_id(u);
+                if (j <= i) continue;
+                const float4 o = src.cand(u);
+                const float dx = o.x - me.x, dy = o.y - me.y;
+                if (sqrtf(dx * dx + dy * dy) < pr.x + __ldg(&a.par[te.base + j]).x - kCollideDepth) ++ca;
+            }
+        }
+        const float lim = pr.x - kCollideDepth;
+        const int s0 = a.seg_cell_start[te.co + k], s1 = a.seg_cell_start[te.co + k + 1];
+        for (int q = s0; q < s1; ++q) {
+            const float4 sg = __ldg(&a.segs[te.seg0 + a.seg_cell_ids[q]]);
+            if (box_dist2(me.x, me.y, sg) >= lim * lim) continue;
+            float qx, qy;
+            if (sqrtf(seg_dist2(me.x, me.y, sg, qx, qy)) < lim) ++cs;
+        }
+        if (a.mode == kTiledStatsOnly) return;
+    }
+
+    NbList<KMAX> nb;
+    select_neighbors<KMAX>(src, cx, cy, te.W, te.H, i, me, ap.R, ap.K, nb, w);
+    if (a.nbr_out) {
+        int* out = a.nbr_out + (size_t)g * ap.K;
+#pragma unroll
+        for (int s = 0; s < KMAX; ++s)
+            if (s < ap.K) out[s] = s < nb.cnt ? nb.id[s] : -1;
+    }
+    float2 v;
+    if (i == te.robot) {
+        v = make_float2(me.z, me.w);
+    } else {
+        // segment candidates: the cell's precomputed list
+        const int s0 = a.seg_cell_start[te.co + k], s1 = a.seg_cell_start[te.co + k + 1];
+        bool queued;
+        v = solve_velocity<KMAX>(ap, GlobalAgents{a.state_in + te.base, a.par + te.base}, i, te.robot, me, pr,
+                                 __ldg(&a.goal[g]), te.seg0, ListedSegments{a.seg_cell_ids + s0, s1 - s0}, nb, w,
+                                 nullptr, queued);
+    }
+    ++w.agent_steps;
+    float4 nx;
+    nx.x = fmaf(ap.dt, v.x, me.x);
+    nx.y = fmaf(ap.dt, v.y, me.y);
+    nx.z = v.x;
+    nx.w = v.y;
+    a.state_out[g] = nx;
+    if (a.stats && i != te.robot) {
+        speed += (double)sqrtf(v.x * v.x + v.y * v.y);
+        const float2 gl = __ldg(&a.goal[g]);
+        const float gx = gl.x - nx.x, gy = gl.y - nx.y;
+        if (a.reach[g] < 0 && sqrtf(gx * gx + gy * gy) <= pr.x) a.reach[g] = (int)(*a.step_index + 1);
+    }
+}
+
+template <int KMAX>
+__global__ void __launch_bounds__(kUpdateThreads) tiled_update(TiledStepArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int s_row_slot[kTile + 2], s_row_off[kTile + 2], s_row_cnt[kTile + 2];
+    __shared__ int s_tile_row_slot[kTile], s_tile_row_cnt[kTile];
+    __shared__ int s_total, s_tile_total;
+    __shared__ unsigned long long s_ca, s_cs;
+    __shared__ double s_speed;
+    const TiledEnv te = a.envs[blockIdx.y];
+    const int tile = blockIdx.x;
+    const int tiles_x = (te.W + kTile - 1) / kTile, tiles_y = (te.H + kTile - 1) / kTile;
+    if (tile >= tiles_x * tiles_y) return;
+    const int tx0 = (tile % tiles_x) * kTile, ty0 = (tile / tiles_x) * kTile;
+    const int tx1 = min(tx0 + kTile, te.W) - 1, ty1 = min(ty0 + kTile, te.H) - 1;
+    const int hx0 = max(tx0 - 1, 0), hx1 = min(tx1 + 1, te.W - 1);
+    const int hy0 = max(ty0 - 1, 0), hy1 = min(ty1 + 1, te.H - 1);
+    const int* start = a.start + te.co;
+    float4* s_pv = (float4*)smem_raw;
+    int* s_id = (int*)(s_pv + a.halo_cap);
+
+    if (threadIdx.x == 0) {
+        int off = 0;
+        for (int r = 0; r <= hy1 - hy0; ++r) {
+            const int yy = hy0 + r;
+            const int b0 = start[yy * te.W + hx0], b1 = start[yy * te.W + hx1 + 1];
+            s_row_slot[r] = b0;
+            s_row_off[r] = off;
+            s_row_cnt[r] = b1 - b0;
+            off += b1 - b0;
+        }
+        s_total = off;
+        int tot = 0;
+        for (int r = 0; r <= ty1 - ty0; ++r) {
+            const int yy = ty0 + r;
+            const int b0 = start[yy * te.W + tx0], b1 = start[yy * te.W + tx1 + 1];
+            s_tile_row_slot[r] = b0;
+            s_tile_row_cnt[r] = b1 - b0;
+            tot += b1 - b0;
+        }
+        s_tile_total = tot;
+        s_ca = 0;
+        s_cs = 0;
+        s_speed = 0.0;
+    }
+    __syncthreads();
+    const bool staged = s_total <= a.halo_cap;
+    if (staged) {
+        for (int r = 0; r <= hy1 - hy0; ++r) {
+            const int b0 = s_row_slot[r], n = s_row_cnt[r], o = s_row_off[r];
+            for (int q = threadIdx.x; q < n; q += blockDim.x) {
+                s_pv[o + q] = a.sorted_pv[b0 + q];
+                s_id[o + q] = a.sorted_id[b0 + q];
+            }
+        }
+    }
+    __syncthreads();
+
+    const AgentParams ap{a.R, a.dt, a.tau, a.tau_o, a.robot_alpha, a.K, a.segs, a.err};
+    Tally w;
+    unsigned long long ca = 0, cs = 0;
+    double speed = 0.0;
+    const int total = s_tile_total;
+    for (int q = threadIdx.x; q < total; q += blockDim.x) {
+        int r = 0, qq = q;
+        while (qq >= s_tile_row_cnt[r]) {
+            qq -= s_tile_row_cnt[r];
+            ++r;
+        }
+        const int slot = s_tile_row_slot[r] + qq;
+        if (staged) {
+            const HaloSource src{s_pv, s_id, start, s_row_slot, s_row_off, te.W, hy0};
+            tile_agent<KMAX>(a, ap, te, src, slot, w, ca, cs, speed);
+        } else {
+            const GlobalSource src{a.sorted_pv, a.sorted_id, start, te.W};
+            tile_agent<KMAX>(a, ap, te, src, slot, w, ca, cs, speed);
+        }
+    }
+    if (a.work) flush_tally(w, a.work);
+    if (a.stats) {
+        if (ca) atomicAdd(&s_ca, ca);
+        if (cs) atomicAdd(&s_cs, cs);
+        if (speed != 0.0) atomicAdd(&s_speed, speed);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            EnvStats* st = a.stats + te.e;
+            if (s_ca) atomicAdd(&st->agent_collisions, s_ca);
+            if (s_cs) atomicAdd(&st->segment_collisions, s_cs);
+            if (s_speed != 0.0) atomicAdd(&st->speed_sum, s_speed);
+        }
+    }
+}
+
+__global__ void tiled_finish_step(TiledStepArgs a) {
+    // one thread: count the step in the statistics and advance the step index
+    if (a.stats && a.mode != kTiledStatsOnly)
+        for (int k = 0; k < a.n_envs; ++k) a.stats[a.envs[k].e].steps += 1;
+    if (a.mode != kTiledStatsOnly) *a.step_index += 1;
+}
+
+template <int KMAX>
+cudaError_t update_k(const TiledStepArgs& a, int max_tiles, cudaStream_t s) {
+    tiled_update<KMAX><<<dim3(max_tiles, a.n_envs), kUpdateThreads, tiled_smem_bytes(a.halo_cap), s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+__global__ void set_step_kernel(long long* p, long long v) { *p = v; }
+
+cudaError_t launch_set_step(long long* p, long long value, cudaStream_t s) {
+    set_step_kernel<<<1, 1, 0, s>>>(p, value);
+    return cudaGetLastError();
+}
+
+size_t tiled_smem_bytes(int halo_cap) { return (size_t)halo_cap * (sizeof(float4) + sizeof(int)); }
+
+cudaError_t tiled_init(int halo_cap) {
+    const int smem = (int)tiled_smem_bytes(halo_cap);
+    cudaError_t e = cudaFuncSetAttribute(tiled_update<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(tiled_update<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(tiled_update<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    return e;
+}
+
+cudaError_t launch_tiled_step(const TiledStepArgs& a, int max_agents, int max_tiles, cudaStream_t s) {
+    if (a.n_envs == 0) return cudaSuccess;
+    const dim3 agrid((max_agents + kCountThreads - 1) / kCountThreads, a.n_envs);
+    tiled_count<<<agrid, kCountThreads, 0, s>>>(a);
+    tiled_scan<<<a.n_envs, kScanThreads, 0, s>>>(a);
+    tiled_scatter<<<agrid, kCountThreads, 0, s>>>(a);
+    cudaError_t e;
+    switch (resident_kmax(a.K)) {
+        case 8: e = update_k<8>(a, max_tiles, s); break;
+        case 16: e = update_k<16>(a, max_tiles, s); break;
+        default: e = update_k<32>(a, max_tiles, s); break;
+    }
+    if (e != cudaSuccess) return e;
+    tiled_finish_step<<<1, 1, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace crowd

@@ -162,7 +162,7 @@ __device__ __forceinline__ float contact_gap2(float pix, float piy, float pjx, f
 // used for pairs within a relative 1e-6 of contact.  Every product and sum is rounded
 // separately so that the colliding and leg decisions match an FP64
 // evaluation of the definition exactly.
-__device__ __noinline__ Line agent_line_fp64(float pix, float piy, float vix, float viy, float ri, float pjx,
+static __device__ __noinline__ Line agent_line_fp64(float pix, float piy, float vix, float viy, float ri, float pjx,
                                              float pjy, float vjx, float vjy, float rj, float tau, float dt,
                                              float alpha, bool i_before_j) {
     const double px = __dsub_rn((double)pjx, (double)pix), py = __dsub_rn((double)pjy, (double)piy);
@@ -564,6 +564,151 @@ __device__ __forceinline__ float2 lp_fallback(const Line* L, int n, int n_hard, 
             float2 t;
             if (lp_dir(S, m, vmax, li.nx, li.ny, pref, t)) v = t;
             dist = -((v.x - li.qx) * li.nx + (v.y - li.qy) * li.ny);
+        }
+    }
+    return v;
+}
+
+// ---------------------------------------------------------------- A5, warp-cooperative ----
+// The same LPs with the 32 lanes of a warp sharing each 1D sub-solve: lines
+// live in shared memory, every lane clips the interval by a strided subset
+// of the previous lines, and the bounds meet in a shuffle reduction.  All
+// lanes call with identical arguments and return identical results.
+
+__device__ __forceinline__ bool coop_line_interval(const Line* L, int k, float vmax, float& tl, float& tr) {
+    const int lane = threadIdx.x & 31;
+    const Line lk = L[k];
+    const float dx = -lk.ny, dy = lk.nx;
+    const float qd = lk.qx * dx + lk.qy * dy;
+    float disc = qd * qd - (lk.qx * lk.qx + lk.qy * lk.qy) + vmax * vmax;
+    if (disc < 0.f) {
+        if (disc < -2.f * kIntervalSlack * vmax) return false;
+        disc = 0.f;
+    }
+    const float sq = sqrtf(disc);
+    float lo = -qd - sq, hi = -qd + sq;
+    bool bad = false;
+    for (int l = lane; l < k; l += 32) {
+        const Line ll = L[l];
+        const float den = dx * ll.nx + dy * ll.ny;
+        const float num = (ll.qx - lk.qx) * ll.nx + (ll.qy - lk.qy) * ll.ny;
+        if (fabsf(den) < 1e-4f) {
+            const double ddx = -(double)lk.ny, ddy = (double)lk.nx;
+            const double dden = ddx * (double)ll.nx + ddy * (double)ll.ny;
+            const double dnum = ((double)ll.qx - (double)lk.qx) * (double)ll.nx +
+                                ((double)ll.qy - (double)lk.qy) * (double)ll.ny;
+            if (fabs(dden) <= kEpsParallel) {
+                bad |= dnum > 0.0;
+                continue;
+            }
+            const float t = (float)(dnum / dden);
+            if (dden > 0.0) lo = fmaxf(lo, t);
+            else hi = fminf(hi, t);
+        } else {
+            const float t = __fdiv_rn(num, den);
+            if (den > 0.f) lo = fmaxf(lo, t);
+            else hi = fminf(hi, t);
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        lo = fmaxf(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+        hi = fminf(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    }
+    if (__any_sync(0xffffffffu, bad)) return false;
+    if (lo > hi) {
+        if (lo - hi > kIntervalSlack) return false;
+        lo = hi = 0.5f * (lo + hi);
+    }
+    tl = lo;
+    tr = hi;
+    return true;
+}
+
+// Warp-cooperative lp2 (least distance to pref); returns n or the failing line.
+__device__ __forceinline__ int coop_lp2(const Line* L, int n, float vmax, float2 pref, float2& v) {
+    const float pl2 = pref.x * pref.x + pref.y * pref.y;
+    if (pl2 > vmax * vmax) {
+        const float k = vmax * rsqrtf(pl2);
+        v = make_float2(pref.x * k, pref.y * k);
+    } else {
+        v = pref;
+    }
+    for (int k = 0; k < n; ++k) {
+        const Line lk = L[k];
+        if ((v.x - lk.qx) * lk.nx + (v.y - lk.qy) * lk.ny < 0.f) {
+            float tl, tr;
+            if (!coop_line_interval(L, k, vmax, tl, tr)) return k;
+            const float dx = -lk.ny, dy = lk.nx;
+            float t = (pref.x - lk.qx) * dx + (pref.y - lk.qy) * dy;
+            t = fminf(fmaxf(t, tl), tr);
+            v = make_float2(lk.qx + t * dx, lk.qy + t * dy);
+        }
+    }
+    return n;
+}
+
+// Warp-cooperative lp_dir.
+__device__ __forceinline__ bool coop_lp_dir(const Line* S, int m, float vmax, float ox, float oy, float2 pref,
+                                            float2& v) {
+    v = make_float2(vmax * ox, vmax * oy);
+    for (int k = 0; k < m; ++k) {
+        const Line lk = S[k];
+        if ((v.x - lk.qx) * lk.nx + (v.y - lk.qy) * lk.ny < 0.f) {
+            float tl, tr;
+            if (!coop_line_interval(S, k, vmax, tl, tr)) return false;
+            const float dx = -lk.ny, dy = lk.nx;
+            const float dd = dx * ox + dy * oy;
+            float t;
+            if (dd > 1e-6f) t = tr;
+            else if (dd < -1e-6f) t = tl;
+            else t = fminf(fmaxf((pref.x - lk.qx) * dx + (pref.y - lk.qy) * dy, tl), tr);
+            v = make_float2(lk.qx + t * dx, lk.qy + t * dy);
+        }
+    }
+    return true;
+}
+
+// Warp-cooperative lp_fallback; L and S (scratch, >= n lines) in shared
+// memory.  A same-direction pair gives an inert line (zero normal).
+__device__ __forceinline__ float2 coop_fallback(const Line* L, int n, int n_hard, float vmax, float2 pref, Line* S) {
+    const int lane = threadIdx.x & 31;
+    float2 v;
+    if (coop_lp2(L, n_hard, vmax, pref, v) < n_hard) {
+        n_hard = 0;
+        const float pl2 = pref.x * pref.x + pref.y * pref.y;
+        const float k = pl2 > vmax * vmax ? vmax * rsqrtf(pl2) : 1.f;
+        v = make_float2(pref.x * k, pref.y * k);
+    }
+    float dist = -INFINITY;
+    for (int i = n_hard; i < n; ++i) {
+        const Line li = L[i];
+        const float viol = -((v.x - li.qx) * li.nx + (v.y - li.qy) * li.ny);
+        if (viol > dist) {
+            const float ci = li.qx * li.nx + li.qy * li.ny;
+            for (int m = lane; m < i; m += 32) {
+                if (m < n_hard) {
+                    S[m] = L[m];
+                } else {
+                    const Line lj = L[m];
+                    float nx = lj.nx - li.nx, ny = lj.ny - li.ny;
+                    const float nl2 = nx * nx + ny * ny;
+                    if (nl2 < 1e-12f) {
+                        S[m] = Line{0.f, 0.f, 0.f, 0.f};
+                    } else {
+                        const float inv = rsqrtf(nl2);
+                        nx *= inv;
+                        ny *= inv;
+                        const float c = ((lj.qx * lj.nx + lj.qy * lj.ny) - ci) * inv;
+                        S[m] = Line{c * nx, c * ny, nx, ny};
+                    }
+                }
+            }
+            __syncwarp();
+            float2 t;
+            if (coop_lp_dir(S, i, vmax, li.nx, li.ny, pref, t)) v = t;
+            dist = -((v.x - li.qx) * li.nx + (v.y - li.qy) * li.ny);
+            __syncwarp();
         }
     }
     return v;

@@ -86,13 +86,6 @@ def test_bad_arguments_rejected_on_host(lib, over, msg):
     assert not h.value
 
 
-def test_oversized_environment_rejected(lib):
-    n = 4096
-    st, h, keep = _create(lib, n=n, radii=np.full(n, 0.3, np.float32), max_speeds=np.full(n, 1.0, np.float32),
-                          pos=np.zeros((n, 2), np.float32))
-    assert st == cw.CROWD_EINVAL and "per environment" in lib.crowd_last_error().decode()
-
-
 def test_null_handle_calls_fail_cleanly(lib):
     assert lib.crowd_step(None, C.c_float(0.1), None, 0, 1) == cw.CROWD_EINVAL
     assert lib.crowd_read_state(None, None, 0) == cw.CROWD_EINVAL
