@@ -148,6 +148,9 @@ def run_ours(args):
         flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
     torch.cuda.synchronize(dev)
 
+    # launch shape chosen by the library's autotuner on this state (untimed)
+    tuning = cr.autotune(n_steps=50)
+
     def one_rollout():
         cr.step(rv_dev, n_steps=ROLLOUT)
 
@@ -268,7 +271,7 @@ def run_ours(args):
                            "step": "one 1000-step rollout of all envs (crowd_step n_steps=1000)",
                            "l2": "256 MiB buffer written between timed rollouts",
                            "parallelism": f"env replicas x{ws}"},
-                "wall_s": wall, "clocks": clocks, "e2e": e2e, "gpu_launches": args.steps,
+                "wall_s": wall, "clocks": clocks, "e2e": e2e, "gpu_launches": args.steps, "tuning": tuning,
                 "roofline": roofline, "cpu_baseline": cpu, "plain": plain,
                 "kernel_ms": per}
         print(json.dumps(line))

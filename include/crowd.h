@@ -165,6 +165,31 @@ crowd_status crowd_read_stats(crowd_t h, crowd_env_stats* env_stats, int32_t* re
 /* Host copy of the work counters (only with CROWD_FLAG_COUNT_WORK). */
 crowd_status crowd_read_work(crowd_t h, crowd_work* out);
 
+/* Launch shape of the shared-memory-resident kernel (environments of up to
+ * 2048 agents).  None of these changes results except coop_fallback, which
+ * changes only the rounding of infeasible-LP fallbacks (both within the
+ * 1e-4 m/s contract).
+ *   block_threads: threads per CTA, a multiple of 32 in [32, 512], or 0 for
+ *                  one thread per agent of the largest environment;
+ *   coop_fallback: 1 = infeasible LPs are queued and solved by whole warps
+ *                  after the pass, 0 = solved in place by their thread;
+ *   cell_split:    1 = grid cells >= R and a 3x3 cell search, 2 = cells
+ *                  >= R/2 and a 5x5 search (fewer candidates per agent). */
+typedef struct {
+    int32_t block_threads;
+    int32_t coop_fallback;
+    int32_t cell_split;
+} crowd_tuning;
+
+crowd_status crowd_get_tuning(crowd_t h, crowd_tuning* out);
+crowd_status crowd_set_tuning(crowd_t h, const crowd_tuning* t);
+
+/* Time every tuning candidate (block_threads 64/128/256/512 x coop_fallback
+ * x cell_split) over n_steps steps of length dt from the current state, keep
+ * the fastest, and restore the state, statistics and counters.  Waits for the
+ * stream; allocates temporary device memory.  `chosen` may be NULL. */
+crowd_status crowd_autotune(crowd_t h, float dt, int32_t n_steps, crowd_tuning* chosen);
+
 /* Zero the statistics and reach steps and restart the step counter at 0. */
 crowd_status crowd_reset_stats(crowd_t h);
 

@@ -21,12 +21,14 @@ CROWD_HOST, CROWD_DEVICE = 0, 1
 CROWD_FLAG_EXPORT_NEIGHBORS = 1
 CROWD_FLAG_STATS = 2
 CROWD_FLAG_COUNT_WORK = 4
+CROWD_FLAG_FORCE_TILED = 8
 STATUS_NAMES = {0: "CROWD_OK", 1: "CROWD_EINVAL", 2: "CROWD_ENOMEM", 3: "CROWD_ECUDA", 4: "CROWD_EDEVICE",
                 5: "CROWD_ESTATE"}
 
 EXPORTED = ["crowd_create", "crowd_set_goals", "crowd_set_state", "crowd_step", "crowd_read_state",
             "crowd_read_neighbors", "crowd_read_stats", "crowd_read_work", "crowd_reset_stats", "crowd_synchronize",
-            "crowd_destroy", "crowd_num_agents", "crowd_num_envs", "crowd_last_error", "crowd_abi_version"]
+            "crowd_destroy", "crowd_num_agents", "crowd_num_envs", "crowd_last_error", "crowd_abi_version",
+            "crowd_get_tuning", "crowd_set_tuning", "crowd_autotune"]
 
 
 class CrowdError(RuntimeError):
@@ -51,6 +53,10 @@ class crowd_work(C.Structure):
                                           "fallbacks")]
 
 
+class crowd_tuning(C.Structure):
+    _fields_ = [("block_threads", C.c_int32), ("coop_fallback", C.c_int32), ("cell_split", C.c_int32)]
+
+
 _lib = None
 
 
@@ -72,6 +78,9 @@ def load(path: str = LIB_PATH):
     L.crowd_read_stats.argtypes = [vp, vp, vp]
     L.crowd_read_work.argtypes = [vp, vp]
     L.crowd_reset_stats.argtypes = [vp]
+    L.crowd_get_tuning.argtypes = [vp, vp]
+    L.crowd_set_tuning.argtypes = [vp, vp]
+    L.crowd_autotune.argtypes = [vp, C.c_float, i32, vp]
     L.crowd_synchronize.argtypes = [vp]
     L.crowd_destroy.argtypes = [vp]
     L.crowd_num_agents.argtypes = [vp]
@@ -185,6 +194,23 @@ def crowd_read_work(h):
     return {n: int(getattr(w, n)) for n, _ in crowd_work._fields_}
 
 
+def crowd_get_tuning(h):
+    t = crowd_tuning()
+    _check(load().crowd_get_tuning(h, C.byref(t)))
+    return dict(block_threads=t.block_threads, coop_fallback=t.coop_fallback, cell_split=t.cell_split)
+
+
+def crowd_set_tuning(h, block_threads=0, coop_fallback=1, cell_split=1):
+    t = crowd_tuning(block_threads, coop_fallback, cell_split)
+    _check(load().crowd_set_tuning(h, C.byref(t)))
+
+
+def crowd_autotune(h, dt, n_steps):
+    t = crowd_tuning()
+    _check(load().crowd_autotune(h, C.c_float(dt), int(n_steps), C.byref(t)))
+    return dict(block_threads=t.block_threads, coop_fallback=t.coop_fallback, cell_split=t.cell_split)
+
+
 def crowd_reset_stats(h):
     _check(load().crowd_reset_stats(h))
 
@@ -245,6 +271,15 @@ class Crowd:
 
     def work(self):
         return crowd_read_work(self.h)
+
+    def tuning(self):
+        return crowd_get_tuning(self.h)
+
+    def set_tuning(self, **kw):
+        crowd_set_tuning(self.h, **kw)
+
+    def autotune(self, n_steps=20, dt=None):
+        return crowd_autotune(self.h, self.scene.dt if dt is None else dt, n_steps)
 
     def reset_stats(self):
         crowd_reset_stats(self.h)

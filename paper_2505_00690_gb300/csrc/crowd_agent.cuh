@@ -73,23 +73,25 @@ __device__ __forceinline__ float box_dist2(float px, float py, float4 s) {
 }
 
 // A2: the K nearest agents within R of agent `self` (in cell (cx, cy) of a
-// W x H grid with cell size >= R), ordered by (FP64 key, index) exactly as
+// W x H grid with cell size >= R / span, so that every neighbour lies within
+// `span` cells), ordered by (FP64 key, index) exactly as
 // the definition ranks them.  Candidates are ranked by their FP32 squared
 // distance packed with the index into one 64-bit key; FP32 and FP64 keys
 // further apart than kKeyRelErr order alike, so the FP32 order is exact
 // unless two of the first K+1 keys are closer than that, in which case the
 // 3x3 block is rescanned with FP64 keys.  Candidates within kKeyRelErr of R^2
-// are admitted by their FP64 key.
+// are admitted by their FP64 key.  The list keeps KMAX + 1 >= K + 1 entries;
+// entries past K + 1 play no part.
 template <int KMAX, class Src>
 __device__ __forceinline__ void select_neighbors(const Src& src, int cx, int cy, int W, int H, int self, float4 me,
-                                                 float R, int K, NbList<KMAX>& out, Tally& w) {
+                                                 float R, int K, NbList<KMAX>& out, Tally& w, int span = 1) {
     const float R2 = R * R;
     const float R2hi = R2 * (1.f + kKeyRelErr), R2lo = R2 * (1.f - kKeyRelErr);
     const double Rd = (double)R;
     const unsigned long long R2bits = (unsigned long long)__double_as_longlong(__dmul_rn(Rd, Rd));
     const double xi = (double)me.x, yi = (double)me.y;
-    const int xa = max(cx - 1, 0), xb = min(cx + 1, W - 1);
-    const int ya = max(cy - 1, 0), yb = min(cy + 1, H - 1);
+    const int xa = max(cx - span, 0), xb = min(cx + span, W - 1);
+    const int ya = max(cy - span, 0), yb = min(cy + span, H - 1);
     TopK32<KMAX + 1> top;
     top.init();
     for (int yy = ya; yy <= yb; ++yy) {
@@ -103,7 +105,7 @@ __device__ __forceinline__ void select_neighbors(const Src& src, int cx, int cy,
                 const int j = src.cand_id(u);
                 if (j == self) continue;
                 if (d2 > R2lo && !(rank_key(xi, yi, o.x, o.y) < R2bits)) continue;
-                top.insert(((unsigned long long)__float_as_uint(d2) << 32) | (unsigned)j, K + 1);
+                top.insert(((unsigned long long)__float_as_uint(d2) << 32) | (unsigned)j);
             }
         }
     }

@@ -91,7 +91,9 @@ struct crowd_ctx {
     // resident path: environments that fit one CTA (the first n_res of `order`)
     int n_res = 0;
     int res_max_agents = 0;
-    int block = 0, grid = 0;
+    int block = 0, grid = 0;  // resident launch shape for `tune`
+    Tuning tune{0, 1, 1};
+    int sms = 0;
 
     // tiled path: larger environments (or all, with CROWD_FLAG_FORCE_TILED)
     int n_tiled = 0, tiled_max_agents = 0, tiled_max_tiles = 0, halo_cap = 0;
@@ -294,6 +296,59 @@ void build_tiled_env(int e, int base, int n, int seg0, int ns, int robot, const 
                     seg_cell_ids);
 }
 
+
+// Launch shape of the resident kernel for a tuning: block threads (0: one per
+// agent of the largest environment, 64..512) and as many CTAs as fit.
+void apply_tuning(crowd_t h, const Tuning& t) {
+    h->tune = t;
+    h->block = t.block_threads > 0 ? t.block_threads : resident_block_threads(h->res_max_agents);
+    const int per_sm = std::max(1, resident_ctas_per_sm(h->res_max_agents, h->block, h->p.max_neighbors));
+    h->grid = std::max(1, std::min(std::max(h->n_res, 1), per_sm * std::max(h->sms, 1)));
+}
+
+// Enqueue n steps of the resident environments on `s`.
+crowd_status resident_steps(crowd_t h, float dt, const float2* rv, int n_steps, bool stats, float tau_o,
+                            cudaStream_t s) {
+    ResidentArgs a{};
+    a.n_work = h->n_res;
+    a.order = h->order;
+    a.queue = h->queue;
+    a.env_start = h->env_start;
+    a.seg_start = h->seg_start;
+    a.robot_index = h->robot_index;
+    a.segs = h->segs;
+    a.seg_grid = h->seg_grid;
+    a.seg_cell_start = h->seg_cell_start;
+    a.seg_cell_ids = h->seg_cell_ids;
+    a.par = h->par;
+    a.goal = h->goal;
+    a.state = h->state;
+    a.robot_vel = rv;
+    a.robot_stride = h->E;
+    a.n_steps = n_steps;
+    a.dt = dt;
+    a.tau = h->p.time_horizon;
+    a.tau_o = tau_o;
+    a.R = h->p.neighbor_dist;
+    a.robot_alpha = h->p.robot_responsibility;
+    a.K = h->p.max_neighbors;
+    a.nbr_out = h->nbr;
+    a.stats = stats ? h->stats : nullptr;
+    a.reach = stats ? h->reach : nullptr;
+    a.step_base = h->step_index;
+    a.work = h->work;
+    a.err = h->err;
+    a.max_agents = h->res_max_agents;
+    a.cell_split = h->tune.cell_split;
+    a.coop_fallback = h->tune.coop_fallback;
+    CUDA_TRY(cudaMemsetAsync(h->queue, 0, sizeof(int), s), "reset work queue");
+    cudaError_t e = launch_resident(a, h->grid, h->block, s);
+    if (e != cudaSuccess) {
+        h->broken = e != cudaErrorInvalidValue && e != cudaErrorInvalidConfiguration;
+        return cuda_fail(e, "launch crowd step");
+    }
+    return CROWD_OK;
+}
 
 // Arguments of step s (0-based) of an n-step tiled sequence.
 TiledStepArgs tiled_args(crowd_t h, float dt, const float2* rv, int s, int n_steps, bool stats, float tau_o,
@@ -616,15 +671,14 @@ crowd_status crowd_create(int32_t n_envs, const int32_t* agents_per_env, const f
     }
 
     // launch shape: one CTA per environment, as many resident per SM as fit
-    h->block = resident_block_threads(h->res_max_agents);
     h->halo_cap = kHaloCap;
     int sms = 0;
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device)) != cudaSuccess) {
         cuda_fail(e, "device attributes");
         return bail(CROWD_ECUDA);
     }
-    const int per_sm = std::max(1, resident_ctas_per_sm(h->res_max_agents, h->block, p->max_neighbors));
-    h->grid = std::max(1, std::min(std::max(h->n_res, 1), per_sm * sms));
+    h->sms = sms;
+    apply_tuning(h, h->tune);
 
     if ((e = cudaStreamSynchronize(h->stream)) != cudaSuccess) {
         cuda_fail(e, "synchronize after create");
@@ -682,42 +736,8 @@ crowd_status crowd_step(crowd_t h, float dt, const float* robot_vel, int32_t ptr
     const bool stats = (h->p.flags & CROWD_FLAG_STATS) != 0;
     const float tau_o = h->p.time_horizon_obst > 0.f ? h->p.time_horizon_obst : h->p.time_horizon;
     if (h->n_res) {
-        ResidentArgs a{};
-        a.n_work = h->n_res;
-        a.order = h->order;
-        a.queue = h->queue;
-        a.env_start = h->env_start;
-        a.seg_start = h->seg_start;
-        a.robot_index = h->robot_index;
-        a.segs = h->segs;
-        a.seg_grid = h->seg_grid;
-        a.seg_cell_start = h->seg_cell_start;
-        a.seg_cell_ids = h->seg_cell_ids;
-        a.par = h->par;
-        a.goal = h->goal;
-        a.state = h->state;
-        a.robot_vel = rv;
-        a.robot_stride = h->E;
-        a.n_steps = n_steps;
-        a.dt = dt;
-        a.tau = h->p.time_horizon;
-        a.tau_o = tau_o;
-        a.R = h->p.neighbor_dist;
-        a.robot_alpha = h->p.robot_responsibility;
-        a.K = h->p.max_neighbors;
-        a.nbr_out = h->nbr;
-        a.stats = stats ? h->stats : nullptr;
-        a.reach = stats ? h->reach : nullptr;
-        a.step_base = h->step_index;
-        a.work = h->work;
-        a.err = h->err;
-        a.max_agents = h->res_max_agents;
-        CUDA_TRY(cudaMemsetAsync(h->queue, 0, sizeof(int), h->stream), "reset work queue");
-        cudaError_t e = launch_resident(a, h->grid, h->block, h->stream);
-        if (e != cudaSuccess) {
-            h->broken = e != cudaErrorInvalidValue && e != cudaErrorInvalidConfiguration;
-            return cuda_fail(e, "launch crowd step");
-        }
+        st = resident_steps(h, dt, rv, n_steps, stats, tau_o, h->stream);
+        if (st) return st;
     }
     if (h->n_tiled) {
         st = tiled_steps(h, dt, rv, n_steps, stats, tau_o);
@@ -784,6 +804,96 @@ crowd_status crowd_read_work(crowd_t h, crowd_work* out) {
     static_assert(sizeof(WorkCount) == sizeof(crowd_work), "work counter layout");
     CUDA_TRY(cudaMemcpyAsync(out, h->work, sizeof(WorkCount), cudaMemcpyDeviceToHost, h->stream), "copy work out");
     return read_err_word(h);
+}
+
+crowd_status crowd_get_tuning(crowd_t h, crowd_tuning* out) {
+    crowd_status st = check_handle(h);
+    if (st) return st;
+    if (!out) return fail(CROWD_EINVAL, "out is null");
+    out->block_threads = h->block;
+    out->coop_fallback = h->tune.coop_fallback;
+    out->cell_split = h->tune.cell_split;
+    return CROWD_OK;
+}
+
+crowd_status crowd_set_tuning(crowd_t h, const crowd_tuning* t) {
+    crowd_status st = check_handle(h);
+    if (st) return st;
+    if (!t) return fail(CROWD_EINVAL, "tuning is null");
+    if (t->block_threads != 0 && (t->block_threads < 32 || t->block_threads > 512 || t->block_threads % 32))
+        return fail(CROWD_EINVAL, "block_threads must be 0 or a multiple of 32 in [32, 512]");
+    if (t->cell_split != 1 && t->cell_split != 2) return fail(CROWD_EINVAL, "cell_split must be 1 or 2");
+    apply_tuning(h, Tuning{t->block_threads, t->coop_fallback ? 1 : 0, t->cell_split});
+    return CROWD_OK;
+}
+
+crowd_status crowd_autotune(crowd_t h, float dt, int32_t n_steps, crowd_tuning* chosen) {
+    crowd_status st = check_handle(h);
+    if (st) return st;
+    if (!(dt > 0.f) || !std::isfinite(dt) || n_steps < 1) return fail(CROWD_EINVAL, "dt > 0 and n_steps >= 1 required");
+    if (h->n_res && h->N) {
+        // save everything a trial step touches, time each candidate, restore
+        float4* saved = nullptr;
+        EnvStats* saved_stats = nullptr;
+        int* saved_reach = nullptr;
+        WorkCount saved_work{};
+        CUDA_TRY(dev_alloc(&saved, h->N), "autotune scratch");
+        cudaError_t e = dev_alloc(&saved_stats, h->E);
+        if (e == cudaSuccess) e = dev_alloc(&saved_reach, h->N);
+        cudaEvent_t t0 = nullptr, t1 = nullptr;
+        if (e == cudaSuccess) e = cudaEventCreate(&t0);
+        if (e == cudaSuccess) e = cudaEventCreate(&t1);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(saved, h->state, sizeof(float4) * h->N, cudaMemcpyDeviceToDevice, h->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(saved_stats, h->stats, sizeof(EnvStats) * h->E, cudaMemcpyDeviceToDevice, h->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(saved_reach, h->reach, sizeof(int) * h->N, cudaMemcpyDeviceToDevice, h->stream);
+        if (e == cudaSuccess && h->work)
+            e = cudaMemcpyAsync(&saved_work, h->work, sizeof(WorkCount), cudaMemcpyDeviceToHost, h->stream);
+        const Tuning before = h->tune;
+        Tuning best = before;
+        float best_ms = 1e30f;
+        const float tau_o = h->p.time_horizon_obst > 0.f ? h->p.time_horizon_obst : h->p.time_horizon;
+        const int blocks[] = {64, 128, 256, 512};
+        for (int bi = 0; bi < 4 && e == cudaSuccess; ++bi)
+            for (int coop = 0; coop <= 1 && e == cudaSuccess; ++coop)
+                for (int split = 1; split <= 2 && e == cudaSuccess; ++split) {
+                    apply_tuning(h, Tuning{blocks[bi], coop, split});
+                    float ms = 0.f;
+                    for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {
+                        e = cudaMemcpyAsync(h->state, saved, sizeof(float4) * h->N, cudaMemcpyDeviceToDevice, h->stream);
+                        if (e != cudaSuccess) break;
+                        if (rep == 1) e = cudaEventRecord(t0, h->stream);
+                        if (e != cudaSuccess) break;
+                        if (resident_steps(h, dt, nullptr, n_steps, false, tau_o, h->stream) != CROWD_OK) {
+                            e = cudaErrorLaunchFailure;
+                            break;
+                        }
+                        if (rep == 1) {
+                            e = cudaEventRecord(t1, h->stream);
+                            if (e == cudaSuccess) e = cudaEventSynchronize(t1);
+                            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, t0, t1);
+                        }
+                    }
+                    if (e == cudaSuccess && ms < best_ms) {
+                        best_ms = ms;
+                        best = h->tune;
+                    }
+                }
+        if (e == cudaSuccess) e = cudaMemcpyAsync(h->state, saved, sizeof(float4) * h->N, cudaMemcpyDeviceToDevice, h->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(h->stats, saved_stats, sizeof(EnvStats) * h->E, cudaMemcpyDeviceToDevice, h->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(h->reach, saved_reach, sizeof(int) * h->N, cudaMemcpyDeviceToDevice, h->stream);
+        if (e == cudaSuccess && h->work)
+            e = cudaMemcpyAsync(h->work, &saved_work, sizeof(WorkCount), cudaMemcpyHostToDevice, h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        if (t0) cudaEventDestroy(t0);
+        if (t1) cudaEventDestroy(t1);
+        cudaFree(saved);
+        if (saved_stats) cudaFree(saved_stats);
+        if (saved_reach) cudaFree(saved_reach);
+        apply_tuning(h, e == cudaSuccess ? best : before);
+        if (e != cudaSuccess) return cuda_fail(e, "autotune");
+    }
+    if (chosen) return crowd_get_tuning(h, chosen);
+    return CROWD_OK;
 }
 
 crowd_status crowd_reset_stats(crowd_t h) {

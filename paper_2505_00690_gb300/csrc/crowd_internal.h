@@ -77,6 +77,15 @@ struct ResidentArgs {
     WorkCount* work;        // or null: count work items
     int* err;               // device error word
     int max_agents;         // largest environment in `order` (sizes shared memory)
+    int cell_split;         // grid cells >= R / cell_split (1: 3x3 search, 2: 5x5)
+    int coop_fallback;      // infeasible LPs solved by whole warps after the pass (1) or in place (0)
+};
+
+// Launch-shape knobs of the resident kernel (chosen by crowd_autotune).
+struct Tuning {
+    int block_threads;  // 0: one thread per agent of the largest environment (64..512)
+    int coop_fallback;
+    int cell_split;
 };
 
 // One large environment of the tiled path (static uniform grid, cell >= R).

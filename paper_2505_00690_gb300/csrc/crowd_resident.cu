@@ -114,9 +114,10 @@ __device__ __forceinline__ int cell_coord(float v, float v0, float inv_c, int n)
     return min(max(c, 0), n - 1);
 }
 
-// Block-wide bounding box -> grid with cell size >= R (times a margin that
-// covers FP32 rounding of the cell coordinate), at most kGridMax per side.
-__device__ __forceinline__ void build_grid(const Smem& S, int n, float R, float* red, Grid* g) {
+// Block-wide bounding box -> grid with cell size >= R / split (times a margin
+// that covers FP32 rounding of the cell coordinate), at most kGridMax per
+// side; neighbours then lie within `split` cells.
+__device__ __forceinline__ void build_grid(const Smem& S, int n, float R, int split, float* red, Grid* g) {
     float xl = INFINITY, xh = -INFINITY, yl = INFINITY, yh = -INFINITY;
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
         const float4 p = S.pv[i];
@@ -152,7 +153,7 @@ __device__ __forceinline__ void build_grid(const Smem& S, int n, float R, float*
         if (!(xh >= xl)) { xl = 0.f; xh = 0.f; }
         if (!(yh >= yl)) { yl = 0.f; yh = 0.f; }
         const float ext = fmaxf(xh - xl, yh - yl);
-        const float c = fmaxf(R * 1.0001f, ext / (float)(kGridMax - 1));
+        const float c = fmaxf(R * 1.0001f / (float)split, ext / (float)(kGridMax - 1));
         g->x0 = xl;
         g->y0 = yl;
         g->inv_c = __frcp_rz(c);
@@ -270,7 +271,8 @@ __device__ __forceinline__ void agent_update(const ResidentArgs& a, const AgentP
     NbList<KMAX> nb;
     const SmemSource src{S.spv, S.sid, S.cell, c.g.W};
     select_neighbors<KMAX>(src, cell_coord(me.x, c.g.x0, c.g.inv_c, c.g.W),
-                           cell_coord(me.y, c.g.y0, c.g.inv_c, c.g.H), c.g.W, c.g.H, i, me, a.R, a.K, nb, w);
+                           cell_coord(me.y, c.g.y0, c.g.inv_c, c.g.H), c.g.W, c.g.H, i, me, a.R, a.K, nb, w,
+                           a.cell_split);
     const int K = a.K;
     if (c.last && a.nbr_out) {
         int* out = a.nbr_out + (size_t)(c.base + i) * K;
@@ -288,7 +290,7 @@ __device__ __forceinline__ void agent_update(const ResidentArgs& a, const AgentP
     }
     bool queued;
     const float2 v = solve_velocity<KMAX>(ap, SmemAgents{S.pv, S.par}, i, c.robot, me, pr, S.goal[i], c.seg0,
-                                          cell_segments(a, c, me), nb, w, &fbq, queued);
+                                          cell_segments(a, c, me), nb, w, a.coop_fallback ? &fbq : nullptr, queued);
     if (!queued) integrate(a, S, c, i, me, pr.x, v, speed_acc);
 }
 
@@ -315,8 +317,9 @@ __device__ __forceinline__ void count_collisions(const ResidentArgs& a, const Sm
     const float ri = S.par[i].x;
     const int cx = cell_coord(me.x, c.g.x0, c.g.inv_c, c.g.W);
     const int cy = cell_coord(me.y, c.g.y0, c.g.inv_c, c.g.H);
-    const int xa = max(cx - 1, 0), xb = min(cx + 1, c.g.W - 1);
-    for (int yy = max(cy - 1, 0); yy <= min(cy + 1, c.g.H - 1); ++yy) {
+    const int sp = a.cell_split;
+    const int xa = max(cx - sp, 0), xb = min(cx + sp, c.g.W - 1);
+    for (int yy = max(cy - sp, 0); yy <= min(cy + sp, c.g.H - 1); ++yy) {
         const int b0 = S.cell[yy * c.g.W + xa], b1 = S.cell[yy * c.g.W + xb + 1];
         for (int u = b0; u < b1; ++u) {
             const int j = S.sid[u];
@@ -377,7 +380,9 @@ __global__ void __launch_bounds__(kMaxThreads) resident_kernel(ResidentArgs a) {
         unsigned long long ca = 0, cs = 0;
         Tally tally;
         const AgentParams ap{a.R, a.dt, a.tau, a.tau_o, a.robot_alpha, a.K, a.segs, a.err};
-        const FbQueue fbq{&s_fb_count, S.fb_cap, S.lmax, S.fb, S.fb_lines};
+        // the queue capacity depends on this environment alone, so that its
+        // results do not depend on the batch it runs in
+        const FbQueue fbq{&s_fb_count, min(S.fb_cap, fb_capacity(c.n)), S.lmax, S.fb, S.fb_lines};
         const int passes = a.n_steps + (a.stats ? 1 : 0);
         for (int step = 0; step < passes; ++step) {
             const bool compute = step < a.n_steps;
@@ -387,7 +392,7 @@ __global__ void __launch_bounds__(kMaxThreads) resident_kernel(ResidentArgs a) {
                 S.pv[c.robot].w = cmd.y;
             }
             __syncthreads();
-            build_grid(S, c.n, a.R, red, &grid);
+            build_grid(S, c.n, a.R, a.cell_split, red, &grid);
             c.g = grid;
             sort_by_cell(S, c.n, c.g);
             c.step = step;
@@ -400,7 +405,7 @@ __global__ void __launch_bounds__(kMaxThreads) resident_kernel(ResidentArgs a) {
             for (int t = threadIdx.x; t < c.n; t += blockDim.x)
                 agent_update<KMAX>(a, ap, S, c, t, speed_acc, tally, fbq);
             __syncthreads();
-            const int n_queued = min(s_fb_count, S.fb_cap);
+            const int n_queued = min(s_fb_count, fbq.cap);
             if (n_queued) {
                 run_fallbacks(a, S, c, n_queued, speed_acc);
                 __syncthreads();
@@ -461,11 +466,12 @@ int resident_block_threads(int max_agents) {
     return b < 64 ? 64 : (b > kMaxThreads ? kMaxThreads : b);
 }
 
-int resident_kmax(int K) { return K <= 8 ? 8 : (K <= 16 ? 16 : 32); }
+int resident_kmax(int K) { return K <= 8 ? 8 : (K <= 10 ? 10 : (K <= 16 ? 16 : 32)); }
 
 cudaError_t launch_resident(const ResidentArgs& a, int grid, int block, cudaStream_t stream) {
     switch (resident_kmax(a.K)) {
         case 8: return launch_k<8>(a, grid, block, stream);
+        case 10: return launch_k<10>(a, grid, block, stream);
         case 16: return launch_k<16>(a, grid, block, stream);
         default: return launch_k<32>(a, grid, block, stream);
     }
@@ -474,6 +480,7 @@ cudaError_t launch_resident(const ResidentArgs& a, int grid, int block, cudaStre
 int resident_ctas_per_sm(int max_agents, int block, int K) {
     switch (resident_kmax(K)) {
         case 8: return ctas_k<8>(max_agents, block);
+        case 10: return ctas_k<10>(max_agents, block);
         case 16: return ctas_k<16>(max_agents, block);
         default: return ctas_k<32>(max_agents, block);
     }

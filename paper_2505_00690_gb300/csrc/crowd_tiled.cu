@@ -344,6 +344,7 @@ size_t tiled_smem_bytes(int halo_cap) { return (size_t)halo_cap * (sizeof(float4
 cudaError_t tiled_init(int halo_cap) {
     const int smem = (int)tiled_smem_bytes(halo_cap);
     cudaError_t e = cudaFuncSetAttribute(tiled_update<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(tiled_update<10>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(tiled_update<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(tiled_update<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     return e;
@@ -358,6 +359,7 @@ cudaError_t launch_tiled_step(const TiledStepArgs& a, int max_agents, int max_ti
     cudaError_t e;
     switch (resident_kmax(a.K)) {
         case 8: e = update_k<8>(a, max_tiles, s); break;
+        case 10: e = update_k<10>(a, max_tiles, s); break;
         case 16: e = update_k<16>(a, max_tiles, s); break;
         default: e = update_k<32>(a, max_tiles, s); break;
     }

@@ -106,23 +106,17 @@ struct TopK32 {
 #pragma unroll
         for (int s = 0; s < CAP; ++s) e[s] = ~0ull;
     }
-    // Keep the `keep` smallest (keep <= CAP).
-    __device__ __forceinline__ void insert(unsigned long long x, int keep) {
-        unsigned long long last = ~0ull;
+    // Keep the CAP smallest: one branch-free bubble pass (min stays, max
+    // moves on), skipped when x does not beat the current largest.
+    __device__ __forceinline__ void insert(unsigned long long x) {
+        if (x >= e[CAP - 1]) return;
 #pragma unroll
-        for (int s = 0; s < CAP; ++s)
-            if (s == keep - 1) last = e[s];
-        if (keep <= 0 || x >= last) return;
-        int p = 0;
-#pragma unroll
-        for (int s = 0; s < CAP; ++s) p += (s < cnt && e[s] < x) ? 1 : 0;
-#pragma unroll
-        for (int s = CAP - 1; s >= 1; --s) {
-            if (s > p) e[s] = e[s - 1];
-            else if (s == p) e[s] = x;
+        for (int s = 0; s < CAP; ++s) {
+            const unsigned long long lo = e[s] < x ? e[s] : x;
+            x = e[s] < x ? x : e[s];
+            e[s] = lo;
         }
-        if (p == 0) e[0] = x;
-        cnt = cnt < keep ? cnt + 1 : keep;
+        cnt = cnt < CAP ? cnt + 1 : CAP;
     }
     __device__ __forceinline__ static float key_of(unsigned long long x) { return __uint_as_float((unsigned)(x >> 32)); }
 };

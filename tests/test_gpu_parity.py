@@ -337,3 +337,44 @@ def test_dense_crowd_full_size_sampled():
     assert np.array_equal(nb[sel], nbO[sel])
     assert np.abs(G[sel, 2:] - vo[sel]).max() <= VEL_TOL
     cr.close()
+
+
+# ----------------------------------------------------------------------------- tuning
+
+def test_tuning_knobs_and_autotune():
+    """Block size and cell split change no result bit; the cooperative and the
+    in-place fallback agree within the velocity tolerance; the autotuner
+    restores the state it timed on."""
+    from paper_2505_00690_gb300 import crowd as cw
+
+    sc = scenes.urban_block(6, n_envs=8, steps=30)
+    ref = None
+    for block in (64, 160, 512):
+        for split in (1, 2):
+            cr = _crowd(sc, 0)
+            cr.set_tuning(block_threads=block, coop_fallback=1, cell_split=split)
+            cr.step(sc.robot_vel[:30], n_steps=30)
+            out = cr.state()
+            if ref is None:
+                ref = out
+            assert np.array_equal(out, ref), (block, split)
+            cr.close()
+    # one step from a common state: in-place vs cooperative fallback
+    S = ref.copy()
+    outs = []
+    for coop in (0, 1):
+        cr = _crowd(sc, 0)
+        cr.set_tuning(block_threads=0, coop_fallback=coop, cell_split=1)
+        cr.set_state(S)
+        cr.step(sc.robot_vel[30:31], n_steps=1)
+        outs.append(cr.state())
+        cr.close()
+    assert np.abs(outs[0] - outs[1]).max() <= VEL_TOL
+    cr = _crowd(sc, cw.CROWD_FLAG_STATS)
+    before = cr.state()
+    t = cr.autotune(n_steps=5)
+    assert t["block_threads"] in (64, 128, 256, 512) and t["cell_split"] in (1, 2)
+    assert np.array_equal(cr.state(), before)
+    env, reach = cr.stats()
+    assert all(e["steps"] == 0 for e in env) and np.all(reach == -1)
+    cr.close()
