@@ -262,6 +262,10 @@ def run_ours(args):
     if rank == 0 and ws == 1 and not args.no_cpu:
         cpu = cpu_baseline(sc, budget_s=args.cpu_seconds)
 
+    serving = None
+    if rank == 0 and args.serve:
+        serving = serve_workload(args.serve_seconds)
+
     cr.close()
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -272,11 +276,32 @@ def run_ours(args):
                            "l2": "256 MiB buffer written between timed rollouts",
                            "parallelism": f"env replicas x{ws}"},
                 "wall_s": wall, "clocks": clocks, "e2e": e2e, "gpu_launches": args.steps, "tuning": tuning,
-                "roofline": roofline, "cpu_baseline": cpu, "plain": plain,
+                "roofline": roofline, "cpu_baseline": cpu, "plain": plain, "serving": serving,
                 "kernel_ms": per}
         print(json.dumps(line))
     if dist:
         tdist.destroy_process_group()
+
+
+def serve_workload(duration_s):
+    """Serving workload: Poisson arrivals at 200 requests/s for duration_s,
+    one environment each (32..2048 agents log-uniform, 0..60 convex polygons,
+    100..1000 steps), through the continuous-batching server (4 GiB budget,
+    1024 slots, 50 steps per tick); plus the plain form (one request at a
+    time, one step per launch) on the first 20 requests."""
+    from paper_2505_00690_gb300 import crowd as cw
+    from paper_2505_00690_gb300 import scenes
+    from paper_2505_00690_gb300 import serve
+
+    reqs = scenes.serving_stream(seed=0, rate=200.0, duration_s=duration_s)
+    sc0 = reqs[0].scene
+    params = cw.params_for(sc0)
+    out = serve.run_stream(reqs, params, sc0.dt, chunk_steps=50, max_slots=1024, mem_budget=4 << 30)
+    out.pop("results", None)
+    plain = serve.run_plain(reqs[:20], params, sc0.dt)
+    out["plain_agent_steps_per_s"] = plain
+    out["rate_req_per_s"] = 200.0
+    return out
 
 
 def cpu_baseline(sc, budget_s=12.0, threads=None):
@@ -346,6 +371,9 @@ def main():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--serve", action="store_true",
+                    help="also replay the serving workload (Poisson request stream) and report p50/p99 latency")
+    ap.add_argument("--serve-seconds", type=float, default=10.0)
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

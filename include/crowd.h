@@ -203,6 +203,64 @@ crowd_status crowd_destroy(crowd_t h);
 int64_t crowd_num_agents(crowd_t h);
 int32_t crowd_num_envs(crowd_t h);
 
+/* ------------------------------------------------------------------------
+ * Serving loop with continuous batching.  Rollout requests (one environment
+ * each, with its own step count) are submitted at any time; crowd_server_tick
+ * admits waiting requests first come first served into free slots while the
+ * device-memory budget allows, advances every live request by up to
+ * chunk_steps steps in one batched launch, and copies finished results back.
+ * A request's result depends only on its own inputs, not on the batch it ran
+ * in.  Not thread-safe.
+ * ------------------------------------------------------------------------ */
+typedef struct crowd_server_ctx* crowd_server_t;
+
+typedef struct {
+    int32_t max_slots;     /* requests resident at once, [1, 65536] */
+    int32_t max_agents;    /* per request, [1, 2048] */
+    int32_t max_segments;  /* per request, >= 0 */
+    int32_t max_steps;     /* per request, >= 1 */
+    size_t mem_budget;     /* bytes of request state admitted at once */
+    int32_t chunk_steps;   /* steps per tick, >= 1 */
+} crowd_server_config;
+
+typedef struct {
+    int32_t n_agents;
+    const float* radii;        /* [n] > 0 */
+    const float* max_speeds;   /* [n] >= 0 */
+    const float* pref_speeds;  /* [n] or NULL (= max_speeds) */
+    const float* init_pos;     /* [n][2]; velocities start at 0 */
+    const float* goals;        /* [n][2] */
+    int32_t robot_index;       /* -1 for none */
+    int32_t n_segments;
+    const float* segments;     /* [n_segments][4] */
+    int32_t n_steps;
+    const float* robot_vel;    /* [n_steps][2] or NULL (robot at rest) */
+} crowd_request;
+
+enum { CROWD_REQ_QUEUED = 0, CROWD_REQ_RUNNING = 1, CROWD_REQ_DONE = 2 };
+
+typedef struct {
+    int32_t waiting;
+    int32_t live;
+    size_t bytes_in_use;
+} crowd_server_stats;
+
+/* Create a server on the current device (allocates its slot arena; all
+ * pointers host).  dt is the step length of every request. */
+crowd_status crowd_server_create(const crowd_params* p, float dt, const crowd_server_config* cfg, void* cuda_stream,
+                                 crowd_server_t* out);
+/* Validate and copy a request (host pointers); its id is written to *id. */
+crowd_status crowd_server_submit(crowd_server_t s, const crowd_request* r, int64_t* id);
+/* Retire the previous tick (waits for it), admit, and enqueue the next chunk.
+ * n_live: requests stepped by this tick; n_finished: requests the previous
+ * tick completed.  Either may be NULL. */
+crowd_status crowd_server_tick(crowd_server_t s, int32_t* n_live, int32_t* n_finished);
+/* Status of a request (CROWD_REQ_*); when done, its final state [n][4] is
+ * copied to out_state (if not NULL) and the request is forgotten. */
+crowd_status crowd_server_poll(crowd_server_t s, int64_t id, float* out_state, int32_t* status);
+crowd_status crowd_server_info(crowd_server_t s, crowd_server_stats* out);
+crowd_status crowd_server_destroy(crowd_server_t s);
+
 /* Message for the calling thread's last failed call ("" if none). */
 const char* crowd_last_error(void);
 

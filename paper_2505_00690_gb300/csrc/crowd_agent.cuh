@@ -160,14 +160,17 @@ struct ListedSegments {
 // speed, 0), goal `gl`, its neighbour list, and the segment candidates
 // `sl` of its environment (whose first segment is seg0).
 // With a queue, an infeasible LP is queued for the warp-cooperative fallback
-// (`queued` set, the returned velocity meaningless); without one, or when it
-// is full, the fallback runs here.
+// (`queued` set, the returned velocity meaningless); when the queue is full,
+// `deferred` is set instead and the caller runs the agent again in a later
+// round (so that every fallback of a queued run takes the same cooperative
+// path, whatever the thread order).  Without a queue the fallback runs here.
 template <int KMAX, class Agents, class SegList>
 __device__ __forceinline__ float2 solve_velocity(const AgentParams& a, const Agents& ag, int i, int robot, float4 me,
                                                  float4 pr, float2 gl, int seg0, const SegList& sl,
                                                  const NbList<KMAX>& nb, Tally& w, const FbQueue* fbq,
-                                                 bool& queued) {
+                                                 bool& queued, bool& deferred) {
     queued = false;
+    deferred = false;
     const float2 pref = pref_velocity(me.x, me.y, gl.x, gl.y, pr.z, a.dt);
     Line L[KMAX + kMaxObstacleLines];
 
@@ -222,8 +225,9 @@ __device__ __forceinline__ float2 solve_velocity(const AgentParams& a, const Age
     float2 v;
     const bool feasible = lp2(L, nl, pr.y, pref, v, solves, solve_lines) == nl;
     if (!feasible) {
-        if (fbq && fbq->push(L, nl, no, pr.y, pref, i, me)) {
-            queued = true;
+        if (fbq) {
+            queued = fbq->push(L, nl, no, pr.y, pref, i, me);
+            deferred = !queued;
         } else {
             Line scratch[KMAX + kMaxObstacleLines];
             v = lp_fallback(L, nl, no, pr.y, pref, scratch);

@@ -130,44 +130,23 @@ struct crowd_ctx {
     }
 };
 
-namespace {
+namespace crowd {
 
-crowd_status check_handle(crowd_t h) {
-    if (!h) return fail(CROWD_EINVAL, "null handle");
-    if (h->broken) return fail(CROWD_ESTATE, "handle is unusable after an earlier CUDA failure");
-    return CROWD_OK;
+// Error reporting shared with the serving loop (crowd_server.cu).
+crowd_status api_fail(crowd_status st, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return st;
 }
-
-// Copy a host or device buffer of `bytes` into the device buffer `dst`.
-crowd_status copy_in(crowd_t h, void* dst, const void* src, size_t bytes, int32_t kind, const char* what) {
-    if (kind != CROWD_HOST && kind != CROWD_DEVICE) return fail(CROWD_EINVAL, "%s: ptr_kind must be 0 or 1", what);
-    if (bytes == 0) return CROWD_OK;
-    cudaError_t e = cudaMemcpyAsync(dst, src, bytes, kind == CROWD_HOST ? cudaMemcpyHostToDevice
-                                                                         : cudaMemcpyDeviceToDevice,
-                                    h->stream);
-    if (e != cudaSuccess) return cuda_fail(e, what);
-    return CROWD_OK;
-}
-
-crowd_status read_err_word(crowd_t h) {
-    int err = 0;
-    CUDA_TRY(cudaMemcpyAsync(&err, h->err, sizeof(int), cudaMemcpyDeviceToHost, h->stream), "read error word");
-    CUDA_TRY(cudaStreamSynchronize(h->stream), "synchronize");
-    if (err) {
-        CUDA_TRY(cudaMemsetAsync(h->err, 0, sizeof(int), h->stream), "clear error word");
-        if (err & kErrObstacleOverflow)
-            return fail(CROWD_EDEVICE, "an agent had more than %d static segments in reach in one step",
-                        kMaxObstacleLines);
-        return fail(CROWD_EDEVICE, "device error word 0x%x", err);
-    }
-    return CROWD_OK;
-}
-
 
 // Largest r + tau_obst v_max over an environment's agents, with a margin.
-double seg_reach(int base, int n, const float* radii, const float* vmax, const crowd_params& p) {
+double seg_reach(int base, int n, const float* radii, const float* vmax, float tau, float tau_obst) {
     double reach = 0.0;
-    const double tau_o = p.time_horizon_obst > 0.f ? p.time_horizon_obst : p.time_horizon;
+    const double tau_o = tau_obst > 0.f ? tau_obst : tau;
     for (int i = 0; i < n; ++i) reach = std::max(reach, (double)radii[base + i] + tau_o * (double)vmax[base + i]);
     return reach * (1.0 + 1e-5) + 1e-6;
 }
@@ -210,7 +189,7 @@ void build_seg_lists(const float* segs, int seg0, int ns, double x0, double y0, 
 // Segment grid of a resident environment: the bounding box of its segments
 // padded by reach, cells of at least reach/2 and at most 64 a side.
 SegGrid build_seg_grid(int base, int n, int seg0, int ns, const float* radii, const float* vmax, const float* segs,
-                       const crowd_params& p, int off, std::vector<int>& seg_cell_start,
+                       float tau, float tau_obst, int off, std::vector<int>& seg_cell_start,
                        std::vector<int>& seg_cell_ids) {
     SegGrid g{};
     g.off = off;
@@ -221,7 +200,7 @@ SegGrid build_seg_grid(int base, int n, int seg0, int ns, const float* radii, co
         build_seg_lists(segs, seg0, 0, 0.0, 0.0, 1.0, 1, 1, 0.0, off, seg_cell_start, seg_cell_ids);
         return g;
     }
-    const double reach = seg_reach(base, n, radii, vmax, p);
+    const double reach = seg_reach(base, n, radii, vmax, tau, tau_obst);
     double x0 = 1e300, y0 = 1e300, x1 = -1e300, y1 = -1e300;
     for (int s = 0; s < ns; ++s) {
         const float* q = segs + 4 * (seg0 + s);
@@ -245,6 +224,42 @@ SegGrid build_seg_grid(int base, int n, int seg0, int ns, const float* radii, co
     build_seg_lists(segs, seg0, ns, x0, y0, cc, g.W, g.H, reach, off, seg_cell_start, seg_cell_ids);
     return g;
 }
+
+}  // namespace crowd
+
+namespace {
+
+crowd_status check_handle(crowd_t h) {
+    if (!h) return fail(CROWD_EINVAL, "null handle");
+    if (h->broken) return fail(CROWD_ESTATE, "handle is unusable after an earlier CUDA failure");
+    return CROWD_OK;
+}
+
+// Copy a host or device buffer of `bytes` into the device buffer `dst`.
+crowd_status copy_in(crowd_t h, void* dst, const void* src, size_t bytes, int32_t kind, const char* what) {
+    if (kind != CROWD_HOST && kind != CROWD_DEVICE) return fail(CROWD_EINVAL, "%s: ptr_kind must be 0 or 1", what);
+    if (bytes == 0) return CROWD_OK;
+    cudaError_t e = cudaMemcpyAsync(dst, src, bytes, kind == CROWD_HOST ? cudaMemcpyHostToDevice
+                                                                         : cudaMemcpyDeviceToDevice,
+                                    h->stream);
+    if (e != cudaSuccess) return cuda_fail(e, what);
+    return CROWD_OK;
+}
+
+crowd_status read_err_word(crowd_t h) {
+    int err = 0;
+    CUDA_TRY(cudaMemcpyAsync(&err, h->err, sizeof(int), cudaMemcpyDeviceToHost, h->stream), "read error word");
+    CUDA_TRY(cudaStreamSynchronize(h->stream), "synchronize");
+    if (err) {
+        CUDA_TRY(cudaMemsetAsync(h->err, 0, sizeof(int), h->stream), "clear error word");
+        if (err & kErrObstacleOverflow)
+            return fail(CROWD_EDEVICE, "an agent had more than %d static segments in reach in one step",
+                        kMaxObstacleLines);
+        return fail(CROWD_EDEVICE, "device error word 0x%x", err);
+    }
+    return CROWD_OK;
+}
+
 
 // Static grid of a tiled environment: the bounding box of its agents' start
 // positions and its segments, padded by R, with cells of at least R (times a
@@ -292,7 +307,8 @@ void build_tiled_env(int e, int base, int n, int seg0, int ns, int robot, const 
     te.W = std::min(kTiledGridMax, (int)((x1 - x0) / cc) + 1);
     te.H = std::min(kTiledGridMax, (int)((y1 - y0) / cc) + 1);
 
-    build_seg_lists(segs, seg0, ns, x0, y0, cc, te.W, te.H, seg_reach(base, n, radii, vmax, p), co, seg_cell_start,
+    build_seg_lists(segs, seg0, ns, x0, y0, cc, te.W, te.H,
+                    seg_reach(base, n, radii, vmax, p.time_horizon, p.time_horizon_obst), co, seg_cell_start,
                     seg_cell_ids);
 }
 
@@ -567,7 +583,8 @@ crowd_status crowd_create(int32_t n_envs, const int32_t* agents_per_env, const f
     int seg_off = total_cells;
     for (int e : order) {
         seg_grids[e] = build_seg_grid(env_start[e], agents_per_env[e], seg_start[e], segs_per_env ? segs_per_env[e] : 0,
-                                      radii, max_speeds, segments, *p, seg_off, seg_cell_start, seg_cell_ids);
+                                      radii, max_speeds, segments, p->time_horizon, p->time_horizon_obst, seg_off,
+                                      seg_cell_start, seg_cell_ids);
         seg_off += seg_grids[e].W * seg_grids[e].H + 1;
     }
     if (seg_cell_ids.empty()) seg_cell_ids.push_back(0);

@@ -79,6 +79,14 @@ struct ResidentArgs {
     int max_agents;         // largest environment in `order` (sizes shared memory)
     int cell_split;         // grid cells >= R / cell_split (1: 3x3 search, 2: 5x5)
     int coop_fallback;      // infeasible LPs solved by whole warps after the pass (1) or in place (0)
+    // Per-environment overrides (all null for a batch handle; set by the
+    // serving loop, whose environments are slots of fixed capacity):
+    const int* env_count;   // [E] agents, instead of env_start differences
+    const int* seg_count;   // [E] segments, instead of seg_start differences
+    const int* env_steps;   // [E] steps of this launch, instead of n_steps
+    const int* env_step0;   // [E] steps already done: robot command of step s is
+                            //     robot_vel[e * rv_env_stride + step0 + s], reach steps offset by step0
+    int rv_env_stride;
 };
 
 // Launch-shape knobs of the resident kernel (chosen by crowd_autotune).
@@ -148,6 +156,20 @@ cudaError_t launch_set_step(long long* p, long long value, cudaStream_t s);
 cudaError_t launch_tiled_step(const TiledStepArgs& a, int max_agents, int max_tiles, cudaStream_t s);
 
 size_t resident_smem_bytes(int max_agents, int K, int block);
+
+}  // namespace crowd
+
+#include <vector>
+
+namespace crowd {
+
+// Host-side construction of the static segment lists (crowd_api.cu).
+double seg_reach(int base, int n, const float* radii, const float* vmax, float tau, float tau_obst);
+void build_seg_lists(const float* segs, int seg0, int ns, double x0, double y0, double cc, int W, int H, double reach,
+                     int off, std::vector<int>& seg_cell_start, std::vector<int>& seg_cell_ids);
+SegGrid build_seg_grid(int base, int n, int seg0, int ns, const float* radii, const float* vmax, const float* segs,
+                       float tau, float tau_obst, int off, std::vector<int>& seg_cell_start,
+                       std::vector<int>& seg_cell_ids);
 int resident_block_threads(int max_agents);
 int resident_kmax(int K);
 // Launch on `stream`; `grid` CTAs pull environments from the queue.

@@ -48,6 +48,7 @@ struct Smem {
     int* cell;     // [kMaxCells + 1] counts, then starts
     unsigned short* key;   // [Nm] cell of each agent
     unsigned short* rank;  // [Nm] rank of each agent inside its cell
+    unsigned char* pend;   // [Nm] agents deferred to the next fallback round
     FbEntry* fb;           // [fb_cap] agents queued for the cooperative fallback
     Line* fb_lines;        // [fb_cap][lmax] their lines
     Line* fb_scratch;      // [warps][lmax] subproblem lines of each warp
@@ -82,6 +83,7 @@ __host__ __device__ inline size_t smem_layout(int max_agents, int kmax, int warp
     unsigned char* cell = take(sizeof(int) * (kMaxCells + 1));
     unsigned char* key = take(sizeof(unsigned short) * nm);
     unsigned char* rank = take(sizeof(unsigned short) * nm);
+    unsigned char* pend = take(nm);
     unsigned char* fb = take(sizeof(FbEntry) * fb_cap);
     unsigned char* fb_lines = take(sizeof(Line) * fb_cap * lmax);
     unsigned char* fb_scratch = take(sizeof(Line) * warps * lmax);
@@ -95,6 +97,7 @@ __host__ __device__ inline size_t smem_layout(int max_agents, int kmax, int warp
         s->cell = (int*)cell;
         s->key = (unsigned short*)key;
         s->rank = (unsigned short*)rank;
+        s->pend = pend;
         s->fb = (FbEntry*)fb;
         s->fb_lines = (Line*)fb_lines;
         s->fb_scratch = (Line*)fb_scratch;
@@ -205,6 +208,7 @@ __device__ __forceinline__ void sort_by_cell(const Smem& S, int n, const Grid& g
 
 struct StepCtx {
     int e, base, n, robot, seg0, ns;
+    long long step_base;  // global index of the first step of this launch
     SegGrid sg;
     int step;  // 0-based step inside this launch
     bool last;  // last step of the launch
@@ -254,15 +258,17 @@ __device__ __forceinline__ void integrate(const ResidentArgs& a, const Smem& S, 
             int* rp = a.reach + c.base + i;
             const float2 gl = S.goal[i];
             const float gx = gl.x - nx.x, gy = gl.y - nx.y;
-            if (*rp < 0 && sqrtf(gx * gx + gy * gy) <= r) *rp = (int)(a.step_base + c.step + 1);
+            if (*rp < 0 && sqrtf(gx * gx + gy * gy) <= r) *rp = (int)(c.step_base + c.step + 1);
         }
     }
 }
 
+// Returns true when the agent's infeasible LP found the fallback queue full
+// (the agent then runs again in the next round).
 template <int KMAX>
-__device__ __forceinline__ void agent_update(const ResidentArgs& a, const AgentParams& ap, const Smem& S,
+__device__ __forceinline__ bool agent_update(const ResidentArgs& a, const AgentParams& ap, const Smem& S,
                                              const StepCtx& c, int t, double& speed_acc, Tally& w,
-                                             const FbQueue& fbq) {
+                                             const FbQueue& fbq, bool export_nbrs) {
     const int i = S.sid[t];
     const float4 me = S.spv[t];
     const float4 pr = S.par[i];
@@ -274,7 +280,7 @@ __device__ __forceinline__ void agent_update(const ResidentArgs& a, const AgentP
                            cell_coord(me.y, c.g.y0, c.g.inv_c, c.g.H), c.g.W, c.g.H, i, me, a.R, a.K, nb, w,
                            a.cell_split);
     const int K = a.K;
-    if (c.last && a.nbr_out) {
+    if (c.last && a.nbr_out && export_nbrs) {
         int* out = a.nbr_out + (size_t)(c.base + i) * K;
 #pragma unroll
         for (int s = 0; s < KMAX; ++s)
@@ -286,12 +292,14 @@ __device__ __forceinline__ void agent_update(const ResidentArgs& a, const AgentP
     ++w.agent_steps;
     if (i == c.robot) {
         integrate(a, S, c, i, me, pr.x, make_float2(me.z, me.w), speed_acc);
-        return;
+        return false;
     }
-    bool queued;
+    bool queued, deferred;
     const float2 v = solve_velocity<KMAX>(ap, SmemAgents{S.pv, S.par}, i, c.robot, me, pr, S.goal[i], c.seg0,
-                                          cell_segments(a, c, me), nb, w, a.coop_fallback ? &fbq : nullptr, queued);
-    if (!queued) integrate(a, S, c, i, me, pr.x, v, speed_acc);
+                                          cell_segments(a, c, me), nb, w, a.coop_fallback ? &fbq : nullptr, queued,
+                                          deferred);
+    if (!queued && !deferred) integrate(a, S, c, i, me, pr.x, v, speed_acc);
+    return deferred;
 }
 
 // The queued fallbacks of this step, one warp per agent.
@@ -349,7 +357,7 @@ __global__ void __launch_bounds__(kMaxThreads) resident_kernel(ResidentArgs a) {
     __shared__ double s_speed;
     Smem S;
     smem_layout(a.max_agents, KMAX, blockDim.x >> 5, &S, smem_raw);
-    __shared__ int s_fb_count;
+    __shared__ int s_fb_count, s_pend;
 
     for (;;) {
         if (threadIdx.x == 0) s_work = atomicAdd(a.queue, 1);
@@ -359,11 +367,14 @@ __global__ void __launch_bounds__(kMaxThreads) resident_kernel(ResidentArgs a) {
         StepCtx c;
         c.e = a.order[w];
         c.base = a.env_start[c.e];
-        c.n = a.env_start[c.e + 1] - c.base;
+        c.n = a.env_count ? a.env_count[c.e] : a.env_start[c.e + 1] - c.base;
         c.robot = a.robot_index[c.e];
         c.seg0 = a.seg_start[c.e];
-        c.ns = a.seg_start[c.e + 1] - c.seg0;
+        c.ns = a.seg_count ? a.seg_count[c.e] : a.seg_start[c.e + 1] - c.seg0;
         c.sg = a.seg_grid[c.e];
+        const int n_steps = a.env_steps ? a.env_steps[c.e] : a.n_steps;
+        const int step0 = a.env_step0 ? a.env_step0[c.e] : 0;
+        c.step_base = a.step_base + step0;
         for (int i = threadIdx.x; i < c.n; i += blockDim.x) {
             S.pv[i] = a.state[c.base + i];
             S.par[i] = __ldg(&a.par[c.base + i]);
@@ -383,11 +394,13 @@ __global__ void __launch_bounds__(kMaxThreads) resident_kernel(ResidentArgs a) {
         // the queue capacity depends on this environment alone, so that its
         // results do not depend on the batch it runs in
         const FbQueue fbq{&s_fb_count, min(S.fb_cap, fb_capacity(c.n)), S.lmax, S.fb, S.fb_lines};
-        const int passes = a.n_steps + (a.stats ? 1 : 0);
+        const int passes = n_steps + (a.stats ? 1 : 0);
         for (int step = 0; step < passes; ++step) {
-            const bool compute = step < a.n_steps;
+            const bool compute = step < n_steps;
             if (compute && c.robot >= 0 && c.robot < c.n && a.robot_vel && threadIdx.x == 0) {
-                const float2 cmd = __ldg(&a.robot_vel[(size_t)step * a.robot_stride + c.e]);
+                const size_t at = a.env_step0 ? (size_t)c.e * a.rv_env_stride + step0 + step
+                                              : (size_t)step * a.robot_stride + c.e;
+                const float2 cmd = __ldg(&a.robot_vel[at]);
                 S.pv[c.robot].z = cmd.x;
                 S.pv[c.robot].w = cmd.y;
             }
@@ -396,18 +409,41 @@ __global__ void __launch_bounds__(kMaxThreads) resident_kernel(ResidentArgs a) {
             c.g = grid;
             sort_by_cell(S, c.n, c.g);
             c.step = step;
-            c.last = step == a.n_steps - 1;
+            c.last = step == n_steps - 1;
             if (a.stats && step > 0)
                 for (int t = threadIdx.x; t < c.n; t += blockDim.x) count_collisions(a, S, c, t, ca, cs);
             if (!compute) break;
-            if (threadIdx.x == 0) s_fb_count = 0;
+            if (threadIdx.x == 0) {
+                s_fb_count = 0;
+                s_pend = 0;
+            }
             __syncthreads();
-            for (int t = threadIdx.x; t < c.n; t += blockDim.x)
-                agent_update<KMAX>(a, ap, S, c, t, speed_acc, tally, fbq);
+            for (int t = threadIdx.x; t < c.n; t += blockDim.x) {
+                const bool def = agent_update<KMAX>(a, ap, S, c, t, speed_acc, tally, fbq, true);
+                S.pend[t] = def ? 1 : 0;
+                if (def) atomicAdd(&s_pend, 1);
+            }
             __syncthreads();
-            const int n_queued = min(s_fb_count, fbq.cap);
-            if (n_queued) {
-                run_fallbacks(a, S, c, n_queued, speed_acc);
+            // cooperative fallbacks; agents that found the queue full run
+            // again, round after round, until every fallback went through it
+            for (int round = 0; round <= c.n; ++round) {
+                const int n_queued = min(s_fb_count, fbq.cap);
+                const int n_pend = s_pend;
+                if (n_queued) run_fallbacks(a, S, c, n_queued, speed_acc);
+                __syncthreads();
+                if (n_pend == 0) break;
+                if (threadIdx.x == 0) {
+                    s_fb_count = 0;
+                    s_pend = 0;
+                }
+                __syncthreads();
+                Tally redo;  // the work of a rerun is not counted twice
+                for (int t = threadIdx.x; t < c.n; t += blockDim.x) {
+                    if (!S.pend[t]) continue;
+                    const bool def = agent_update<KMAX>(a, ap, S, c, t, speed_acc, redo, fbq, false);
+                    S.pend[t] = def ? 1 : 0;
+                    if (def) atomicAdd(&s_pend, 1);
+                }
                 __syncthreads();
             }
             float4* tmp = S.pv;
@@ -427,7 +463,7 @@ __global__ void __launch_bounds__(kMaxThreads) resident_kernel(ResidentArgs a) {
                 st->agent_collisions += s_ca;
                 st->segment_collisions += s_cs;
                 st->speed_sum += s_speed;
-                st->steps += (unsigned long long)a.n_steps;
+                st->steps += (unsigned long long)n_steps;
             }
         }
         __syncthreads();

@@ -205,10 +205,10 @@ __device__ __forceinline__ void tile_agent(const TiledStepArgs& a, const AgentPa
     } else {
         // segment candidates: the cell's precomputed list
         const int s0 = a.seg_cell_start[te.co + k], s1 = a.seg_cell_start[te.co + k + 1];
-        bool queued;
+        bool queued, deferred;
         v = solve_velocity<KMAX>(ap, GlobalAgents{a.state_in + te.base, a.par + te.base}, i, te.robot, me, pr,
                                  __ldg(&a.goal[g]), te.seg0, ListedSegments{a.seg_cell_ids + s0, s1 - s0}, nb, w,
-                                 nullptr, queued);
+                                 nullptr, queued, deferred);
     }
     ++w.agent_steps;
     float4 nx;
