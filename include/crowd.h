@@ -94,7 +94,7 @@ typedef struct {
 /* Maximum number of neighbours K. */
 #define CROWD_MAX_NEIGHBORS 32
 /* Maximum number of segment half-planes for one agent in one step. */
-#define CROWD_MAX_OBSTACLE_LINES 32
+#define CROWD_MAX_OBSTACLE_LINES 64
 
 typedef struct {
     float time_horizon;         /* tau > 0, seconds (agents) */

@@ -13,7 +13,7 @@ enum : int {
     kErrTooManyCells = 2,      // internal: grid larger than the shared-memory cell table
 };
 
-constexpr int kMaxObstacleLines = 32;
+constexpr int kMaxObstacleLines = 64;
 // Penetration depth (m) from which two agents, or an agent and a segment,
 // count as colliding in the statistics: 1 mm, well above the FP32 resolution
 // of positions (about 4 um at 40 m), so that agents ORCA leaves exactly

@@ -55,11 +55,12 @@ struct Smem {
     int fb_cap, lmax;
 };
 
-// Fallback queue capacity: about 1/16 of the agents, 8..32 (the urban block
-// has ~2.5% infeasible LPs per step; overflow falls back per thread).
+// Fallback queue capacity: about 1/16 of the agents, 8..16 (the urban block
+// has ~2.5% infeasible LPs per step; agents that find it full run again in
+// another cooperative round).
 __host__ __device__ inline int fb_capacity(int max_agents) {
     const int c = (max_agents + 15) / 16;
-    return c < 8 ? 8 : (c > 32 ? 32 : c);
+    return c < 8 ? 8 : (c > 16 ? 16 : c);
 }
 
 __host__ __device__ inline int round_up4(int n) { return (n + 3) & ~3; }

@@ -405,6 +405,9 @@ __device__ __forceinline__ Line obstacle_line(float px, float py, float vx, floa
 // point) is taken as the single point it is in exact arithmetic, instead of
 // sending an LP that FP32 rounding alone made infeasible to the fallback.
 constexpr float kIntervalSlack = 1e-5f;
+// disc / v_max^2 at or below which a line counts as tangent to the speed disk
+// (a few times the FP32 rounding of disc).
+constexpr float kTangentDisc = 2e-6f;
 
 // Interval [tl, tr] of the parameter t along line k (point q_k + t d_k,
 // d_k = (-n_y, n_x)) inside the speed disk and the lines 0..k-1; false if
@@ -421,6 +424,11 @@ __device__ __forceinline__ bool line_interval(const Line* L, int k, float vmax, 
         if (disc < -2.f * kIntervalSlack * vmax) return false;
         disc = 0.f;
     }
+    // a line tangent to the disk (an overlapping agent's segment line capped
+    // at -v_max is tangent by construction) meets it in one point; FP32
+    // rounding of the line would open a chord of half-length sqrt(disc), so
+    // chords within the rounding of disc are closed
+    if (disc <= kTangentDisc * vmax * vmax) disc = 0.f;
     const float sq = sqrtf(disc);
     tl = -qd - sq;
     tr = -qd + sq;
@@ -579,6 +587,7 @@ __device__ __forceinline__ bool coop_line_interval(const Line* L, int k, float v
         if (disc < -2.f * kIntervalSlack * vmax) return false;
         disc = 0.f;
     }
+    if (disc <= kTangentDisc * vmax * vmax) disc = 0.f;
     const float sq = sqrtf(disc);
     float lo = -qd - sq, hi = -qd + sq;
     bool bad = false;
