@@ -261,6 +261,42 @@ crowd_status crowd_server_poll(crowd_server_t s, int64_t id, float* out_state, i
 crowd_status crowd_server_info(crowd_server_t s, crowd_server_stats* out);
 crowd_status crowd_server_destroy(crowd_server_t s);
 
+/* ------------------------------------------------------------------------
+ * Allocation-free step.  The paper has no counterpart: this entry point is
+ * for callers that cannot call cudaMalloc -- code running inside another
+ * framework's memory pool or under a fixed device-memory budget, real-time
+ * loops that must not allocate after start-up, plug-ins handed only raw
+ * device pointers.  It advances ONE environment by one step with the tiled
+ * kernels and keeps every intermediate buffer (cell keys, ranks, counts and
+ * starts, the state in cell order, per-cell segment lists) in one fixed
+ * file-scope device array of about 7 MB that every GPU loading the library
+ * holds until the process exits.  It calls no cudaMalloc, cudaFree or other
+ * allocating routine.
+ *   - Limits: n_agents <= CROWD_NOALLOC_MAX_AGENTS; the grid over `box`
+ *     (cells of at least neighbor_dist, at most 256 a side) <=
+ *     CROWD_NOALLOC_MAX_CELLS cells; segment-cell list entries <=
+ *     CROWD_NOALLOC_MAX_SEGMENT_CELLS.  Larger inputs fail with CROWD_EINVAL.
+ *   - All calls share the array and it keeps the last call's contents: each
+ *     call clears what must start at zero, but calls whose GPU work overlaps
+ *     (other streams, other host threads) race on it -- serialise them.
+ *   - The first call on a device looks up the array's address with that
+ *     device current and sets a kernel attribute; make it before any stream
+ *     capture.  Each call waits once for the stream (to check the size of the
+ *     segment lists).
+ *   - Device pointers: state_in [n][4] (px, py, vx, vy; the robot slot moves
+ *     with the velocity stored there), state_out [n][4] (must not alias
+ *     state_in), agent_params [n][4] (r, v_max, preferred speed, unused),
+ *     goals [n][2], segments [n_segments][4] (zero-length segments are
+ *     ignored).  Host pointers: box [4] (x0, y0, x1, y1), the region the grid
+ *     covers (agents outside it are still handled exactly), and p.
+ *   - Results match crowd_step on a handle holding the same environment. */
+#define CROWD_NOALLOC_MAX_AGENTS 65536
+#define CROWD_NOALLOC_MAX_CELLS 65536
+#define CROWD_NOALLOC_MAX_SEGMENT_CELLS (1 << 20)
+crowd_status crowd_step_noalloc(int32_t n_agents, const float* state_in, float* state_out, const float* agent_params,
+                                const float* goals, int32_t robot_index, int32_t n_segments, const float* segments,
+                                const float* box, const crowd_params* p, float dt, void* cuda_stream);
+
 /* Message for the calling thread's last failed call ("" if none). */
 const char* crowd_last_error(void);
 

@@ -1,0 +1,103 @@
+"""crowd_step_noalloc, the allocation-free entry point, against crowd_step.
+
+Callers that cannot allocate device memory (inside another framework's
+memory pool, under a fixed budget, in loops that must not allocate after
+start-up) use crowd_step_noalloc, whose scratch lives in a fixed device array
+of the library.  Here it is called through the C ABI twice in a row (the
+second call starting from the first one's output) and compared, call by
+call, with the regular handle-based crowd_step on the same environment.
+"""
+import ctypes as C
+
+import numpy as np
+import pytest
+
+from paper_2505_00690_gb300 import scenes
+
+pytestmark = pytest.mark.gpu
+
+VEL_TOL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def lib():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2505_00690_gb300 import build
+    from paper_2505_00690_gb300 import crowd as cw
+
+    build.build()
+    L = cw.load()
+    vp = C.c_void_p
+    L.crowd_step_noalloc.argtypes = [C.c_int32, vp, vp, vp, vp, C.c_int32, C.c_int32, vp, vp,
+                                     C.POINTER(cw.crowd_params), C.c_float, vp]
+    L.crowd_step_noalloc.restype = C.c_int
+    return L
+
+
+def _box(sc):
+    pts = np.concatenate([sc.pos, sc.goal, sc.segments[:, :2], sc.segments[:, 2:]]) if sc.segments.size else \
+        np.concatenate([sc.pos, sc.goal])
+    lo, hi = pts.min(0) - 1.0, pts.max(0) + 1.0
+    return np.array([lo[0], lo[1], hi[0], hi[1]], np.float32)
+
+
+@pytest.mark.parametrize("which", ["urban_block", "dense_patch"])
+def test_noalloc_matches_crowd_step_two_calls(lib, which):
+    import torch
+
+    from paper_2505_00690_gb300 import crowd as cw
+
+    if which == "urban_block":
+        sc = scenes.urban_block(7, n_envs=1, steps=2)
+    else:
+        sc = scenes.dense_crowd(3, n_envs=1, n_peds=3000, side=40.0, n_segs=30, steps=2)
+    n = sc.n_agents
+    robot = int(sc.robot_index[0])
+    rv = sc.robot_vel[:2] if sc.robot_vel is not None else np.zeros((2, 1, 2), np.float32)
+
+    # regular entry point: a handle, two calls of one step
+    h = cw.Crowd(sc, flags=0)
+    ref = []
+    for k in range(2):
+        h.step(rv[k:k + 1] if sc.robot_vel is not None else None, n_steps=1)
+        ref.append(h.state())
+    h.close()
+
+    # allocation-free entry point: same inputs, device buffers owned by the caller
+    dev = torch.device("cuda")
+    state = torch.from_numpy(sc.state()).to(dev)
+    par = torch.from_numpy(np.stack([sc.radius, sc.max_speed, sc.pref_speed, np.zeros(n, np.float32)], 1)).to(dev)
+    goal = torch.from_numpy(np.ascontiguousarray(sc.goal)).to(dev)
+    segs = torch.from_numpy(np.ascontiguousarray(sc.segments.reshape(-1, 4))).to(dev) if sc.segments.size else None
+    box = _box(sc)
+    params = cw.params_for(sc)
+    outs = [torch.empty_like(state), torch.empty_like(state)]
+    src = state
+    for k in range(2):
+        if robot >= 0:
+            src[robot, 2:] = torch.from_numpy(rv[k, 0]).to(dev)  # the robot moves with the velocity in its slot
+        st = lib.crowd_step_noalloc(n, src.data_ptr(), outs[k].data_ptr(), par.data_ptr(), goal.data_ptr(), robot,
+                                    int(sc.segs_per_env[0]), None if segs is None else segs.data_ptr(),
+                                    box.ctypes.data, C.byref(params), C.c_float(sc.dt), None)
+        assert st == 0, lib.crowd_last_error().decode()
+        torch.cuda.synchronize()
+        got = outs[k].cpu().numpy()
+        assert np.abs(got[:, 2:] - ref[k][:, 2:]).max() <= VEL_TOL, k
+        assert np.abs(got[:, :2] - ref[k][:, :2]).max() <= sc.dt * VEL_TOL + 1e-5, k
+        src = outs[k].clone()
+
+
+def test_noalloc_rejects_oversize(lib):
+    from paper_2505_00690_gb300 import crowd as cw
+
+    params = cw.crowd_params(2.0, 2.0, 5.0, 10, 0.5, 0)
+    box = np.array([0, 0, 10, 10], np.float32)
+    st = lib.crowd_step_noalloc(70000, 1, 1, 1, 1, -1, 0, None, box.ctypes.data, C.byref(params), C.c_float(0.1),
+                                None)
+    assert st == cw.CROWD_EINVAL and "allocation-free" in lib.crowd_last_error().decode()
+    wide = np.array([0, 0, 1e6, 10], np.float32)  # 256 x 1 cells: fine; the agent limit still applies
+    st = lib.crowd_step_noalloc(0, None, None, None, None, -1, 0, None, wide.ctypes.data, C.byref(params),
+                                C.c_float(0.1), None)
+    assert st == 0
