@@ -362,6 +362,31 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def profile_case(which):
+    """Small launches for ncu captures: `resident` = one 20-step launch of the
+    256-env urban block (after one warm launch); `tiled` = two single steps of
+    one 20,000-agent dense-crowd environment (the second is captured)."""
+    from paper_2505_00690_gb300 import build as B
+    from paper_2505_00690_gb300 import crowd as cw
+    from paper_2505_00690_gb300 import scenes
+
+    B.build()
+    if which == "resident":
+        sc = scenes.urban_block(0, steps=20)
+        cr = cw.Crowd(sc)
+        cr.step(sc.robot_vel[:20], n_steps=20)
+        cr.set_state(sc.state())
+        cr.step(sc.robot_vel[:20], n_steps=20)
+    else:
+        sc = scenes.dense_crowd(0, n_envs=1, steps=4)
+        cr = cw.Crowd(sc)
+        cr.step(n_steps=1)
+        cr.step(n_steps=1)
+    cr.synchronize()
+    cr.close()
+    print(json.dumps({"profile_case": which, "agents": sc.n_agents}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -374,8 +399,12 @@ def main():
     ap.add_argument("--serve", action="store_true",
                     help="also replay the serving workload (Poisson request stream) and report p50/p99 latency")
     ap.add_argument("--serve-seconds", type=float, default=10.0)
+    ap.add_argument("--profile-case", choices=["resident", "tiled"], default=None,
+                    help="run a small case for an ncu capture and exit")
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.profile_case:
+        profile_case(args.profile_case)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

@@ -258,6 +258,10 @@ crowd_status crowd_server_tick(crowd_server_t s, int32_t* n_live, int32_t* n_fin
 /* Status of a request (CROWD_REQ_*); when done, its final state [n][4] is
  * copied to out_state (if not NULL) and the request is forgotten. */
 crowd_status crowd_server_poll(crowd_server_t s, int64_t id, float* out_state, int32_t* status);
+/* Ids of up to `cap` requests completed since the last call (oldest first);
+ * *n receives how many were written.  Their results stay available to
+ * crowd_server_poll. */
+crowd_status crowd_server_finished(crowd_server_t s, int64_t* ids, int32_t cap, int32_t* n);
 crowd_status crowd_server_info(crowd_server_t s, crowd_server_stats* out);
 crowd_status crowd_server_destroy(crowd_server_t s);
 

@@ -111,6 +111,7 @@ struct crowd_server_ctx {
     std::map<int64_t, Req> reqs;
     std::vector<int64_t> slot_req;  // request in each slot (0: free)
     std::vector<int> finishing;     // slots whose request ends with the tick in flight
+    std::vector<int64_t> finished;  // requests completed and not yet reported by crowd_server_finished
 
     ~crowd_server_ctx() {
         if (tick_done) cudaEventDestroy(tick_done);
@@ -148,6 +149,7 @@ crowd_status finish_tick(crowd_server_t s) {
         std::memcpy(r.result.data(), s->h_result + (size_t)k * s->cfg.max_agents, sizeof(float4) * r.n);
         r.status = CROWD_REQ_DONE;
         r.slot = -1;
+        s->finished.push_back(r.id);
         s->bytes_in_use -= r.bytes;
         s->slot_req[k] = 0;
     }
@@ -454,6 +456,19 @@ crowd_status crowd_server_poll(crowd_server_t s, int64_t id, float* out_state, i
         if (out_state) std::memcpy(out_state, r.result.data(), sizeof(float) * r.result.size());
         s->reqs.erase(it);
     }
+    return CROWD_OK;
+}
+
+crowd_status crowd_server_finished(crowd_server_t s, int64_t* ids, int32_t cap, int32_t* n) {
+    if (!s || !n || (cap > 0 && !ids)) return api_fail(CROWD_EINVAL, "null argument");
+    if (s->tick_in_flight && cudaEventQuery(s->tick_done) == cudaSuccess) {
+        crowd_status st = finish_tick(s);
+        if (st) return st;
+    }
+    const int32_t k = (int32_t)std::min<size_t>((size_t)std::max(cap, 0), s->finished.size());
+    for (int32_t q = 0; q < k; ++q) ids[q] = s->finished[q];
+    s->finished.erase(s->finished.begin(), s->finished.begin() + k);
+    *n = k;
     return CROWD_OK;
 }
 

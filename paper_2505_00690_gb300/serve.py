@@ -42,9 +42,10 @@ def _lib():
         L.crowd_server_tick.argtypes = [vp, C.POINTER(i32), C.POINTER(i32)]
         L.crowd_server_poll.argtypes = [vp, C.c_int64, vp, C.POINTER(i32)]
         L.crowd_server_info.argtypes = [vp, vp]
+        L.crowd_server_finished.argtypes = [vp, vp, i32, C.POINTER(i32)]
         L.crowd_server_destroy.argtypes = [vp]
         for n in ("crowd_server_create", "crowd_server_submit", "crowd_server_tick", "crowd_server_poll",
-                  "crowd_server_info", "crowd_server_destroy"):
+                  "crowd_server_info", "crowd_server_destroy", "crowd_server_finished"):
             getattr(L, n).restype = C.c_int
         L._server_bound = True
     return L
@@ -92,6 +93,13 @@ class Server:
                                            C.byref(st)))
         return st.value, (out if st.value == CROWD_REQ_DONE else None)
 
+    def finished(self, cap=4096):
+        """Ids of requests completed since the last call."""
+        ids = np.empty(cap, np.int64)
+        n = C.c_int32()
+        cw._check(_lib().crowd_server_finished(self.h, ids.ctypes.data, cap, C.byref(n)))
+        return ids[:n.value].tolist()
+
     def info(self):
         s = crowd_server_stats()
         cw._check(_lib().crowd_server_info(self.h, C.byref(s)))
@@ -134,15 +142,13 @@ def run_stream(requests, params, dt, chunk_steps=50, max_slots=1024, mem_budget=
             nxt += 1
         live, _ = srv.tick()
         max_live = max(max_live, live)
-        for rid in list(pending):
-            k = pending[rid]
-            st, out = srv.poll(rid, requests[k].scene.n_agents)
-            if st == CROWD_REQ_DONE:
-                latency[k] = (time.perf_counter() - t0) / time_scale - requests[k].arrival_s
-                if keep_results:
-                    results[k] = out
-                del pending[rid]
-                done += 1
+        for rid in srv.finished():
+            k = pending.pop(rid)
+            latency[k] = (time.perf_counter() - t0) / time_scale - requests[k].arrival_s
+            st, out = srv.poll(rid, requests[k].scene.n_agents if keep_results else None)
+            if keep_results:
+                results[k] = out
+            done += 1
         if not pending and nxt < len(order):
             # idle until the next arrival
             wait = requests[order[nxt]].arrival_s - (time.perf_counter() - t0) / time_scale
