@@ -172,20 +172,28 @@ crowd_status crowd_read_work(crowd_t h, crowd_work* out);
  *   block_threads: threads per CTA, a multiple of 32 in [32, 512], or 0 for
  *                  one thread per agent of the largest environment;
  *   coop_fallback: 1 = infeasible LPs are queued and solved by whole warps
- *                  after the pass, 0 = solved in place by their thread;
+ *                  after the pass, 0 = solved in place by their thread
+ *                  (the default);
  *   cell_split:    1 = grid cells >= R and a 3x3 cell search, 2 = cells
- *                  >= R/2 and a 5x5 search (fewer candidates per agent). */
+ *                  >= R/2 and a 5x5 search (fewer candidates per agent);
+ *   lanes_per_agent: 1, 2, 4 or 8 lanes of a warp share each agent's work
+ *                  (neighbour candidates, half-planes, LP intervals); with
+ *                  more than one, fallbacks run in place; 0 means 1.
+ * block_threads 0 means one group of lanes per agent of the largest
+ * environment, at most 512 threads. */
 typedef struct {
     int32_t block_threads;
     int32_t coop_fallback;
     int32_t cell_split;
+    int32_t lanes_per_agent;
 } crowd_tuning;
 
 crowd_status crowd_get_tuning(crowd_t h, crowd_tuning* out);
 crowd_status crowd_set_tuning(crowd_t h, const crowd_tuning* t);
 
-/* Time every tuning candidate (block_threads 64/128/256/512 x coop_fallback
- * x cell_split) over n_steps steps of length dt from the current state, keep
+/* Time every tuning candidate (one lane per agent: block_threads
+ * 64/128/256/512 x coop_fallback x cell_split; 2, 4 and 8 lanes per agent: the
+ * default block and 512 threads x cell_split) over n_steps steps of length dt from the current state, keep
  * the fastest, and restore the state, statistics and counters.  Waits for the
  * stream; allocates temporary device memory.  `chosen` may be NULL. */
 crowd_status crowd_autotune(crowd_t h, float dt, int32_t n_steps, crowd_tuning* chosen);

@@ -19,6 +19,7 @@ LIB = os.path.join(BUILD, "libcrowd.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
+              "-prec-div=false", "-prec-sqrt=false",
               "-I", INCLUDE, "-I", CSRC]
 
 
@@ -36,15 +37,24 @@ def _deps():
         glob.glob(os.path.join(INCLUDE, "*.h"))
 
 
-def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+STAMP = os.path.join(BUILD, "flags.txt")
+
+
+def _flags_text(extra=()):
+    return " ".join([nvcc(), *ARCH, *NVCC_FLAGS, *extra])
+
+
+def up_to_date(extra=()) -> bool:
+    if not os.path.exists(LIB) or not os.path.exists(STAMP):
+        return False
+    if open(STAMP).read() != _flags_text(extra):
         return False
     t = os.path.getmtime(LIB)
     return all(os.path.getmtime(f) <= t for f in _deps())
 
 
 def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
-    if not force and up_to_date():
+    if not force and up_to_date(extra_flags):
         return LIB
     os.makedirs(BUILD, exist_ok=True)
     srcs = sources()
@@ -68,6 +78,8 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
     os.replace(tmp, LIB)
+    with open(STAMP, "w") as f:
+        f.write(_flags_text(extra_flags))
     return LIB
 
 

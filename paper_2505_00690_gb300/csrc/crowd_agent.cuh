@@ -74,17 +74,23 @@ __device__ __forceinline__ float box_dist2(float px, float py, float4 s) {
 
 // A2: the K nearest agents within R of agent `self` (in cell (cx, cy) of a
 // W x H grid with cell size >= R / span, so that every neighbour lies within
-// `span` cells), ordered by (FP64 key, index) exactly as
-// the definition ranks them.  Candidates are ranked by their FP32 squared
-// distance packed with the index into one 64-bit key; FP32 and FP64 keys
-// further apart than kKeyRelErr order alike, so the FP32 order is exact
-// unless two of the first K+1 keys are closer than that, in which case the
-// 3x3 block is rescanned with FP64 keys.  Candidates within kKeyRelErr of R^2
-// are admitted by their FP64 key.  The list keeps KMAX + 1 >= K + 1 entries;
-// entries past K + 1 play no part.
+// `span` cells), ordered by (FP64 key, index) exactly as the definition
+// ranks them.
+//
+// Candidates are ranked by their FP32 squared distance packed with their
+// slot in the candidate source into one 64-bit key (the index is loaded only
+// for the K kept, and for candidates at distance 0, which may be the agent
+// itself).  FP32 and FP64 keys further apart than kKeyRelErr order alike, so
+// the FP32 order is exact except inside runs of consecutive keys closer than
+// that ("near ties"); such runs among the first K + 1 are re-sorted by
+// (FP64 key, index), computed for their members only.  A run that reaches the
+// end of a full list may continue past it: then the block of cells is
+// rescanned with FP64 keys.  Candidates within kKeyRelErr of R^2 are admitted
+// by their FP64 key.  The list keeps KMAX + 2 >= K + 2 entries.
 template <int KMAX, class Src>
 __device__ __forceinline__ void select_neighbors(const Src& src, int cx, int cy, int W, int H, int self, float4 me,
                                                  float R, int K, NbList<KMAX>& out, Tally& w, int span = 1) {
+    constexpr int CAP = KMAX + 2;
     const float R2 = R * R;
     const float R2hi = R2 * (1.f + kKeyRelErr), R2lo = R2 * (1.f - kKeyRelErr);
     const double Rd = (double)R;
@@ -92,52 +98,113 @@ __device__ __forceinline__ void select_neighbors(const Src& src, int cx, int cy,
     const double xi = (double)me.x, yi = (double)me.y;
     const int xa = max(cx - span, 0), xb = min(cx + span, W - 1);
     const int ya = max(cy - span, 0), yb = min(cy + span, H - 1);
-    TopK32<KMAX + 1> top;
+    TopK32<CAP> top;
     top.init();
     for (int yy = ya; yy <= yb; ++yy) {
         const int2 r = src.row(yy, xa, xb);
         w.candidates += (unsigned long long)(r.y - r.x);
+        // the next candidate is loaded while this one is ranked
+        float4 nxt = r.x < r.y ? src.cand(r.x) : make_float4(0.f, 0.f, 0.f, 0.f);
         for (int u = r.x; u < r.y; ++u) {
-            const float4 o = src.cand(u);
+            const float4 o = nxt;
+            if (u + 1 < r.y) nxt = src.cand(u + 1);
             const float dx = o.x - me.x, dy = o.y - me.y;
             const float d2 = dx * dx + dy * dy;
             if (d2 < R2hi) {
-                const int j = src.cand_id(u);
-                if (j == self) continue;
+                if (d2 == 0.f && src.cand_id(u) == self) continue;
                 if (d2 > R2lo && !(rank_key(xi, yi, o.x, o.y) < R2bits)) continue;
-                top.insert(((unsigned long long)__float_as_uint(d2) << 32) | (unsigned)j);
+                top.insert(((unsigned long long)__float_as_uint(d2) << 32) | (unsigned)u);
             }
         }
     }
-    bool near_tie = false;
+    const int cnt = top.cnt;
+    // tie[s]: keys s and s + 1 are near-equal (s + 1 < cnt)
+    bool any_tie = false;
+    unsigned tie = 0u;
 #pragma unroll
-    for (int s = 0; s < KMAX; ++s) {
-        if (s < K && s + 1 < top.cnt) {
-            const float ka = TopK32<KMAX + 1>::key_of(top.e[s]), kb = TopK32<KMAX + 1>::key_of(top.e[s + 1]);
-            if (kb - ka <= kKeyRelErr * kb) near_tie = true;
+    for (int s = 0; s + 1 < CAP; ++s) {
+        if (s + 1 < cnt && s < K) {
+            const float ka = TopK32<CAP>::key_of(top.e[s]), kb = TopK32<CAP>::key_of(top.e[s + 1]);
+            if (kb - ka <= kKeyRelErr * kb) {
+                tie |= 1u << s;
+                any_tie = true;
+            }
         }
     }
-    if (!near_tie) {
-        out.cnt = min(top.cnt, K);
+    if (!any_tie) {
+        out.cnt = min(cnt, K);
 #pragma unroll
-        for (int s = 0; s < KMAX; ++s) out.id[s] = (int)(unsigned)(top.e[s] & 0xffffffffull);
+        for (int s = 0; s < KMAX; ++s) out.id[s] = s < out.cnt ? src.cand_id((int)(unsigned)top.e[s]) : -1;
         return;
     }
-    TopK64<KMAX> nb;
-    nb.init();
-    for (int yy = ya; yy <= yb; ++yy) {
-        const int2 r = src.row(yy, xa, xb);
-        for (int u = r.x; u < r.y; ++u) {
-            const int j = src.cand_id(u);
-            if (j == self) continue;
-            const float4 o = src.cand(u);
-            const unsigned long long k = rank_key(xi, yi, o.x, o.y);
-            if (k < R2bits) nb.insert(k, j, K);
+    // extend the run through position K - 1 to its end
+    int e = min(cnt, K) - 1;
+    if (e >= 0 && (tie >> e) & 1u) {
+#pragma unroll
+        for (int s = 0; s + 1 < CAP; ++s) {
+            if (s >= e && s + 1 < cnt && s + 1 == e + 1) {
+                const float ka = TopK32<CAP>::key_of(top.e[s]), kb = TopK32<CAP>::key_of(top.e[s + 1]);
+                if (kb - ka <= kKeyRelErr * kb) {
+                    tie |= 1u << s;
+                    e = s + 1;
+                }
+            }
         }
     }
-    out.cnt = nb.cnt;
+    if (e == CAP - 1 && cnt == CAP) {
+        // the run may continue past the list: rescan with FP64 keys
+        TopK64<KMAX> nb;
+        nb.init();
+        for (int yy = ya; yy <= yb; ++yy) {
+            const int2 r = src.row(yy, xa, xb);
+            for (int u = r.x; u < r.y; ++u) {
+                const int j = src.cand_id(u);
+                if (j == self) continue;
+                const float4 o = src.cand(u);
+                const unsigned long long k = rank_key(xi, yi, o.x, o.y);
+                if (k < R2bits) nb.insert(k, j, K);
+            }
+        }
+        out.cnt = nb.cnt;
 #pragma unroll
-    for (int s = 0; s < KMAX; ++s) out.id[s] = nb.id[s];
+        for (int s = 0; s < KMAX; ++s) out.id[s] = nb.id[s];
+        return;
+    }
+    // positions 0..e: FP64 keys for the members of runs, then each run sorted
+    // by (FP64 key, index) in place
+    unsigned long long kk[CAP];
+    int id[CAP];
+#pragma unroll
+    for (int s = 0; s < CAP; ++s) {
+        kk[s] = 0ull;
+        id[s] = -1;
+        if (s <= e) {
+            const int u = (int)(unsigned)top.e[s];
+            id[s] = src.cand_id(u);
+            const bool member = ((tie >> s) & 1u) || (s > 0 && ((tie >> (s - 1)) & 1u));
+            if (member) {
+                const float4 o = src.cand(u);
+                kk[s] = rank_key(xi, yi, o.x, o.y);
+            }
+        }
+    }
+#pragma unroll 1
+    for (int s = 1; s <= e; ++s) {
+        if (!((tie >> (s - 1)) & 1u)) continue;
+        for (int q = s; q > 0 && ((tie >> (q - 1)) & 1u) &&
+                        TopK64<CAP>::less(kk[q], id[q], kk[q - 1], id[q - 1]);
+             --q) {
+            const unsigned long long tk = kk[q];
+            kk[q] = kk[q - 1];
+            kk[q - 1] = tk;
+            const int ti = id[q];
+            id[q] = id[q - 1];
+            id[q - 1] = ti;
+        }
+    }
+    out.cnt = min(cnt, K);
+#pragma unroll
+    for (int s = 0; s < KMAX; ++s) out.id[s] = s < out.cnt ? id[s] : -1;
 }
 
 // Segment candidates of an agent: all segments of its environment, or a
@@ -207,8 +274,9 @@ __device__ __forceinline__ float2 solve_velocity(const AgentParams& a, const Age
     for (int k = 0; k < no; ++k)
         L[k] = obstacle_line(me.x, me.y, me.z, me.w, pr.x, pr.y, __ldg(&a.segs[seg0 + oid[k]]), a.tau_o, a.dt);
 
-    // A3: one reciprocal half-plane per neighbour, in list order
-#pragma unroll
+    // A3: one reciprocal half-plane per neighbour, in list order (a rolled
+    // loop: one copy of agent_line keeps the kernel's code small)
+#pragma unroll 1
     for (int s = 0; s < KMAX; ++s) {
         if (s < nb.cnt) {
             const int j = nb.id[s];

@@ -91,8 +91,9 @@ struct crowd_ctx {
     // resident path: environments that fit one CTA (the first n_res of `order`)
     int n_res = 0;
     int res_max_agents = 0;
+    int res_max_work = 0;  // largest count of solved (non-robot) agents of a resident environment
     int block = 0, grid = 0;  // resident launch shape for `tune`
-    Tuning tune{0, 1, 1};
+    Tuning tune{0, 0, 1, 1};
     int sms = 0;
 
     // tiled path: larger environments (or all, with CROWD_FLAG_FORCE_TILED)
@@ -317,8 +318,13 @@ void build_tiled_env(int e, int base, int n, int seg0, int ns, int robot, const 
 // agent of the largest environment, 64..512) and as many CTAs as fit.
 void apply_tuning(crowd_t h, const Tuning& t) {
     h->tune = t;
-    h->block = t.block_threads > 0 ? t.block_threads : resident_block_threads(h->res_max_agents);
-    const int per_sm = std::max(1, resident_ctas_per_sm(h->res_max_agents, h->block, h->p.max_neighbors));
+    // default: one thread per agent, or one group of lanes per solved agent
+    // (the robot is integrated apart in that mode)
+    h->block = t.block_threads > 0 ? t.block_threads
+               : t.lanes == 1      ? resident_block_threads(h->res_max_agents)
+                                   : resident_block_threads(std::min(std::max(h->res_max_work, 1) * t.lanes, 512));
+    const int per_sm =
+        std::max(1, resident_ctas_per_sm(h->res_max_agents, h->block, h->p.max_neighbors, t.lanes));
     h->grid = std::max(1, std::min(std::max(h->n_res, 1), per_sm * std::max(h->sms, 1)));
 }
 
@@ -356,7 +362,8 @@ crowd_status resident_steps(crowd_t h, float dt, const float2* rv, int n_steps, 
     a.err = h->err;
     a.max_agents = h->res_max_agents;
     a.cell_split = h->tune.cell_split;
-    a.coop_fallback = h->tune.coop_fallback;
+    a.coop_fallback = h->tune.lanes == 1 ? h->tune.coop_fallback : 0;
+    a.lanes = h->tune.lanes;
     CUDA_TRY(cudaMemsetAsync(h->queue, 0, sizeof(int), s), "reset work queue");
     cudaError_t e = launch_resident(a, h->grid, h->block, s);
     if (e != cudaSuccess) {
@@ -564,7 +571,11 @@ crowd_status crowd_create(int32_t n_envs, const int32_t* agents_per_env, const f
     }
     std::stable_sort(order.begin(), order.end(),
                      [&](int a, int b) { return agents_per_env[a] > agents_per_env[b]; });
-    for (int e : order) h->res_max_agents = std::max(h->res_max_agents, (int)agents_per_env[e]);
+    for (int e : order) {
+        h->res_max_agents = std::max(h->res_max_agents, (int)agents_per_env[e]);
+        const bool has_robot = robot[e] >= 0 && robot[e] < agents_per_env[e];
+        h->res_max_work = std::max(h->res_max_work, (int)agents_per_env[e] - (has_robot ? 1 : 0));
+    }
     h->n_res = (int)order.size();
     h->n_tiled = (int)tiled.size();
     std::vector<int> seg_cell_start, seg_cell_ids;
@@ -830,6 +841,7 @@ crowd_status crowd_get_tuning(crowd_t h, crowd_tuning* out) {
     out->block_threads = h->block;
     out->coop_fallback = h->tune.coop_fallback;
     out->cell_split = h->tune.cell_split;
+    out->lanes_per_agent = h->tune.lanes;
     return CROWD_OK;
 }
 
@@ -840,7 +852,10 @@ crowd_status crowd_set_tuning(crowd_t h, const crowd_tuning* t) {
     if (t->block_threads != 0 && (t->block_threads < 32 || t->block_threads > 512 || t->block_threads % 32))
         return fail(CROWD_EINVAL, "block_threads must be 0 or a multiple of 32 in [32, 512]");
     if (t->cell_split != 1 && t->cell_split != 2) return fail(CROWD_EINVAL, "cell_split must be 1 or 2");
-    apply_tuning(h, Tuning{t->block_threads, t->coop_fallback ? 1 : 0, t->cell_split});
+    const int lanes = t->lanes_per_agent == 0 ? 1 : t->lanes_per_agent;
+    if (lanes != 1 && lanes != 2 && lanes != 4 && lanes != 8)
+        return fail(CROWD_EINVAL, "lanes_per_agent must be 1, 2, 4 or 8");
+    apply_tuning(h, Tuning{t->block_threads, t->coop_fallback ? 1 : 0, t->cell_split, lanes});
     return CROWD_OK;
 }
 
@@ -869,11 +884,22 @@ crowd_status crowd_autotune(crowd_t h, float dt, int32_t n_steps, crowd_tuning* 
         Tuning best = before;
         float best_ms = 1e30f;
         const float tau_o = h->p.time_horizon_obst > 0.f ? h->p.time_horizon_obst : h->p.time_horizon;
+        // candidates: one lane per agent with every block size and fallback
+        // mode; groups of 4 and 8 lanes with a block of one group per agent
+        // (capped at 512 threads) or 512 threads
+        std::vector<Tuning> cands;
         const int blocks[] = {64, 128, 256, 512};
-        for (int bi = 0; bi < 4 && e == cudaSuccess; ++bi)
-            for (int coop = 0; coop <= 1 && e == cudaSuccess; ++coop)
-                for (int split = 1; split <= 2 && e == cudaSuccess; ++split) {
-                    apply_tuning(h, Tuning{blocks[bi], coop, split});
+        for (int bi = 0; bi < 4; ++bi)
+            for (int coop = 0; coop <= 1; ++coop)
+                for (int split = 1; split <= 2; ++split) cands.push_back(Tuning{blocks[bi], coop, split, 1});
+        for (int lanes : {2, 4, 8})
+            for (int split = 1; split <= 2; ++split) {
+                cands.push_back(Tuning{0, 0, split, lanes});
+                cands.push_back(Tuning{512, 0, split, lanes});
+            }
+        for (size_t ci = 0; ci < cands.size() && e == cudaSuccess; ++ci) {
+                {
+                    apply_tuning(h, cands[ci]);
                     float ms = 0.f;
                     for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {
                         e = cudaMemcpyAsync(h->state, saved, sizeof(float4) * h->N, cudaMemcpyDeviceToDevice, h->stream);
@@ -895,6 +921,7 @@ crowd_status crowd_autotune(crowd_t h, float dt, int32_t n_steps, crowd_tuning* 
                         best = h->tune;
                     }
                 }
+        }
         if (e == cudaSuccess) e = cudaMemcpyAsync(h->state, saved, sizeof(float4) * h->N, cudaMemcpyDeviceToDevice, h->stream);
         if (e == cudaSuccess) e = cudaMemcpyAsync(h->stats, saved_stats, sizeof(EnvStats) * h->E, cudaMemcpyDeviceToDevice, h->stream);
         if (e == cudaSuccess) e = cudaMemcpyAsync(h->reach, saved_reach, sizeof(int) * h->N, cudaMemcpyDeviceToDevice, h->stream);

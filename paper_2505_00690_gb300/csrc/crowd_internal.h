@@ -79,6 +79,7 @@ struct ResidentArgs {
     int max_agents;         // largest environment in `order` (sizes shared memory)
     int cell_split;         // grid cells >= R / cell_split (1: 3x3 search, 2: 5x5)
     int coop_fallback;      // infeasible LPs solved by whole warps after the pass (1) or in place (0)
+    int lanes;              // lanes per agent: 1, 2, 4 or 8 (groups of lanes share an agent's work)
     // Per-environment overrides (all null for a batch handle; set by the
     // serving loop, whose environments are slots of fixed capacity):
     const int* env_count;   // [E] agents, instead of env_start differences
@@ -91,9 +92,10 @@ struct ResidentArgs {
 
 // Launch-shape knobs of the resident kernel (chosen by crowd_autotune).
 struct Tuning {
-    int block_threads;  // 0: one thread per agent of the largest environment (64..512)
-    int coop_fallback;
+    int block_threads;  // 0: one group of lanes per agent of the largest environment (64..512 threads)
+    int coop_fallback;  // only with one lane per agent
     int cell_split;
+    int lanes;          // lanes per agent: 1, 2, 4 or 8
 };
 
 // One large environment of the tiled path (static uniform grid, cell >= R).
@@ -175,6 +177,12 @@ int resident_kmax(int K);
 // Launch on `stream`; `grid` CTAs pull environments from the queue.
 cudaError_t launch_resident(const ResidentArgs& a, int grid, int block, cudaStream_t stream);
 // CTAs of the resident kernel that fit on one SM for this configuration.
-int resident_ctas_per_sm(int max_agents, int block, int K);
+int resident_ctas_per_sm(int max_agents, int block, int K, int lanes);
+cudaError_t launch_resident_lanes2(const ResidentArgs& a, int grid, int block, cudaStream_t stream);
+cudaError_t launch_resident_lanes4(const ResidentArgs& a, int grid, int block, cudaStream_t stream);
+cudaError_t launch_resident_lanes8(const ResidentArgs& a, int grid, int block, cudaStream_t stream);
+int resident_ctas_lanes2(int max_agents, int block, int K);
+int resident_ctas_lanes4(int max_agents, int block, int K);
+int resident_ctas_lanes8(int max_agents, int block, int K);
 
 }  // namespace crowd

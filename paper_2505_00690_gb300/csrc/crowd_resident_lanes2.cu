@@ -1,0 +1,13 @@
+// Instantiation of the resident crowd kernel with 2 lanes per agent (its own
+// translation unit so that the instantiations compile in parallel).
+#include "crowd_resident_impl.cuh"
+
+namespace crowd {
+
+cudaError_t launch_resident_lanes2(const ResidentArgs& a, int grid, int block, cudaStream_t stream) {
+    return launch_lanes<2>(a, grid, block, stream);
+}
+
+int resident_ctas_lanes2(int max_agents, int block, int K) { return ctas_lanes<2>(max_agents, block, K); }
+
+}  // namespace crowd

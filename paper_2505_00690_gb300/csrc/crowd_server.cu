@@ -412,14 +412,15 @@ crowd_status crowd_server_tick(crowd_server_t s, int32_t* n_live, int32_t* n_fin
     a.err = s->err;
     a.max_agents = max_agents;
     a.cell_split = 1;
-    a.coop_fallback = 1;
+    a.coop_fallback = 0;
+    a.lanes = 1;
     a.env_count = s->env_count;
     a.seg_count = s->seg_count;
     a.env_steps = s->env_steps;
     a.env_step0 = s->env_step0;
     a.rv_env_stride = c.max_steps;
     const int block = resident_block_threads(max_agents);
-    const int per_sm = std::max(1, resident_ctas_per_sm(max_agents, block, a.K));
+    const int per_sm = std::max(1, resident_ctas_per_sm(max_agents, block, a.K, 1));
     const int grid = std::max(1, std::min(L, per_sm * s->sms));
     cudaError_t e = launch_resident(a, grid, block, s->stream);
     if (e != cudaSuccess) {

@@ -20,7 +20,13 @@
 namespace crowd {
 
 constexpr float kEpsGoal = 1e-6f;  // preferred velocity is 0 closer than this to the goal
-constexpr double kEpsParallel = 1e-9;  // |det(n_k, n_l)| at or below: parallel lines
+
+// Reciprocal and quotients: the library is built with -prec-div=false and
+// -prec-sqrt=false, so FP32 division, reciprocal and square root are the
+// hardware approximations (about 1 ulp).  The contract needs FP32-level
+// accuracy, not correctly rounded results; FP64 and the compensated
+// sums are unaffected.
+__device__ __forceinline__ float __frcp_fast(float x) { return 1.0f / x; }
 
 // Half-plane {v : (v - q) . n >= 0}, n a unit vector.
 struct Line {
@@ -35,8 +41,8 @@ __device__ __forceinline__ float2 pref_velocity(float px, float py, float gx, fl
     float dx = gx - px, dy = gy - py;
     float dist = sqrtf(dx * dx + dy * dy);
     if (dist < kEpsGoal) return make_float2(0.f, 0.f);
-    if (dist <= speed * dt) return make_float2(__fdiv_rn(dx, dt), __fdiv_rn(dy, dt));
-    float k = __fdiv_rn(speed, dist);
+    if (dist <= speed * dt) return make_float2(dx / dt, dy / dt);
+    float k = speed / dist;
     return make_float2(k * dx, k * dy);
 }
 
@@ -106,16 +112,18 @@ struct TopK32 {
 #pragma unroll
         for (int s = 0; s < CAP; ++s) e[s] = ~0ull;
     }
-    // Keep the CAP smallest: one branch-free bubble pass (min stays, max
-    // moves on), skipped when x does not beat the current largest.
+    // Keep the CAP smallest.  Every slot compares with x at once (the list is
+    // sorted, so "greater than x" holds for a suffix of the slots): slot s
+    // takes its left neighbour when that one is greater than x, x when it is
+    // the first greater slot, else keeps its value.  No slot waits on another.
     __device__ __forceinline__ void insert(unsigned long long x) {
         if (x >= e[CAP - 1]) return;
+        bool gt[CAP];
 #pragma unroll
-        for (int s = 0; s < CAP; ++s) {
-            const unsigned long long lo = e[s] < x ? e[s] : x;
-            x = e[s] < x ? x : e[s];
-            e[s] = lo;
-        }
+        for (int s = 0; s < CAP; ++s) gt[s] = e[s] > x;
+#pragma unroll
+        for (int s = CAP - 1; s >= 1; --s) e[s] = gt[s - 1] ? e[s - 1] : (gt[s] ? x : e[s]);
+        e[0] = gt[0] ? x : e[0];
         cnt = cnt < CAP ? cnt + 1 : CAP;
     }
     __device__ __forceinline__ static float key_of(unsigned long long x) { return __uint_as_float((unsigned)(x >> 32)); }
@@ -250,14 +258,14 @@ __device__ __forceinline__ Line agent_line(float pix, float piy, float vix, floa
     const bool apart = gap2 > 0.f;
     float ux, uy, nx, ny;
     if (apart) {
-        const float inv_tau = __frcp_rn(tau);
-        const float wx = vx - __fdiv_rn(px, tau), wy = vy - __fdiv_rn(py, tau);
+        const float inv_tau = __frcp_fast(tau);
+        const float wx = vx - px / tau, wy = vy - py / tau;
         const float w2 = wx * wx + wy * wy;
         const float wp = wx * px + wy * py;
         if (wp < 0.f && wp * wp > r2 * w2) {
             // nearest boundary point on the cut-off arc of D(p/tau, r/tau)
             const float wl = sqrtf(w2);
-            const float inv = __frcp_rn(wl);
+            const float inv = __frcp_fast(wl);
             const float wnx = wx * inv, wny = wy * inv;
             const float m = r * inv_tau - wl;
             ux = m * wnx;
@@ -267,7 +275,7 @@ __device__ __forceinline__ Line agent_line(float pix, float piy, float vix, floa
         } else {
             // nearest boundary point on a leg (ray from 0 tangent to D(p, r))
             const float leg = sqrtf(gap2);
-            const float inv_d2 = __frcp_rn(dist2);
+            const float inv_d2 = __frcp_fast(dist2);
             float det = px * wy - py * wx;
             const float scale = fabsf(px * wy) + fabsf(py * wx);
             bool left = det > 0.f;
@@ -297,11 +305,11 @@ __device__ __forceinline__ Line agent_line(float pix, float piy, float vix, floa
         }
     } else {
         // already overlapping: leave D(p/dt, r/dt) within this step
-        const float wx = vx - __fdiv_rn(px, dt), wy = vy - __fdiv_rn(py, dt);
+        const float wx = vx - px / dt, wy = vy - py / dt;
         const float wl = sqrtf(wx * wx + wy * wy);
         float wnx, wny;
         if (wl > 0.f) {
-            const float inv = __frcp_rn(wl);
+            const float inv = __frcp_fast(wl);
             wnx = wx * inv;
             wny = wy * inv;
         } else if (dist2 > 0.f) {
@@ -312,7 +320,7 @@ __device__ __forceinline__ Line agent_line(float pix, float piy, float vix, floa
             wnx = i_before_j ? 1.f : -1.f;
             wny = 0.f;
         }
-        const float m = __fdiv_rn(r, dt) - wl;
+        const float m = r / dt - wl;
         ux = m * wnx;
         uy = m * wny;
         nx = wnx;
@@ -346,7 +354,7 @@ __device__ __forceinline__ float seg_dist2(float px, float py, float4 s, float& 
     const float ax = s.x - px, ay = s.y - py;
     const float ex = s.z - s.x, ey = s.w - s.y;
     const float e2 = ex * ex + ey * ey;
-    const float t = __fdiv_rn(-(ax * ex + ay * ey), e2);
+    const float t = -(ax * ex + ay * ey) / e2;
     if (t <= 0.f) {
         cx = ax;
         cy = ay;
@@ -354,7 +362,7 @@ __device__ __forceinline__ float seg_dist2(float px, float py, float4 s, float& 
         cx = s.z - px;
         cy = s.w - py;
     } else {
-        const float k = __fdiv_rn(det2(ax, ay, ex, ey), e2);
+        const float k = det2(ax, ay, ex, ey) / e2;
         cx = k * ey;
         cy = -k * ex;
     }
@@ -374,7 +382,7 @@ __device__ __forceinline__ Line obstacle_line(float px, float py, float vx, floa
     const float d = sqrtf(d2);
     float mx, my;
     if (d > 0.f) {
-        const float inv = __frcp_rn(d);
+        const float inv = __frcp_fast(d);
         mx = cx * inv;
         my = cy * inv;
     } else {
@@ -387,9 +395,9 @@ __device__ __forceinline__ Line obstacle_line(float px, float py, float vx, floa
     }
     float b;
     if (d > r) {
-        b = __fdiv_rn(d - r, tau_o);
+        b = (d - r) / tau_o;
     } else {
-        b = fmaxf(__fdiv_rn(d - r, dt), -vmax);
+        b = fmaxf((d - r) / dt, -vmax);
     }
     Line L;
     L.qx = b * mx;
@@ -409,11 +417,49 @@ constexpr float kIntervalSlack = 1e-5f;
 // (a few times the FP32 rounding of disc).
 constexpr float kTangentDisc = 2e-6f;
 
+// |det(n_k, n_l)| at or below which two lines count as parallel.
+constexpr float kEpsParallelF = 1e-9f;
+
+// p + e = a * b exactly (the FMA gives the rounding error of the product).
+__device__ __forceinline__ void two_prod(float a, float b, float& p, float& e) {
+    p = a * b;
+    e = fmaf(a, b, -p);
+}
+
+// Clip [lo, hi] on line k by a line l nearly parallel to it (|det| < 1e-4 in
+// plain FP32, where det and the offset cancel).  det(n_k, n_l) and
+// (q_l - q_k).n_l are evaluated in compensated FP32: exact differences
+// (two_sum) and products (two_prod), summed with their error terms, so both
+// are accurate to a few units of 2^-48 of their terms, as close as an FP64
+// evaluation of the same FP32 inputs for the parallel test (|det| <= 1e-9)
+// and the signs it decides.  GB300 runs FP64 at 1/64 of the FP32 rate, so
+// this branch stays in FP32.  Returns true when l is parallel to k and
+// excludes it entirely.
+__device__ __forceinline__ bool clip_near_parallel(const Line& lk, const Line& ll, float& lo, float& hi) {
+    float p1, e1, p2, e2, den, e3;
+    two_prod(-lk.ny, ll.nx, p1, e1);
+    two_prod(lk.nx, ll.ny, p2, e2);
+    two_sum(p1, p2, den, e3);
+    den += (e1 + e2) + e3;
+    float ax, axe, ay, aye;
+    two_sum(ll.qx, -lk.qx, ax, axe);
+    two_sum(ll.qy, -lk.qy, ay, aye);
+    float q1, f1, q2, f2, num, f3;
+    two_prod(ax, ll.nx, q1, f1);
+    two_prod(ay, ll.ny, q2, f2);
+    two_sum(q1, q2, num, f3);
+    num += ((f1 + f2) + f3) + (axe * ll.nx + aye * ll.ny);
+    if (fabsf(den) <= kEpsParallelF) return num > 0.f;
+    const float t = num / den;
+    if (den > 0.f) lo = fmaxf(lo, t);
+    else hi = fminf(hi, t);
+    return false;
+}
+
 // Interval [tl, tr] of the parameter t along line k (point q_k + t d_k,
 // d_k = (-n_y, n_x)) inside the speed disk and the lines 0..k-1; false if
 // empty by more than kIntervalSlack.  Near-parallel pairs (|det| < 1e-4 in
-// FP32) are classified and intersected in FP64, parallel meaning
-// |det| <= 1e-9.
+// FP32) go through clip_near_parallel, parallel meaning |det| <= 1e-9.
 __device__ __forceinline__ bool line_interval(const Line* L, int k, float vmax, float& tl, float& tr) {
     const Line lk = L[k];
     const float dx = -lk.ny, dy = lk.nx;
@@ -437,19 +483,9 @@ __device__ __forceinline__ bool line_interval(const Line* L, int k, float vmax, 
         const float den = dx * ll.nx + dy * ll.ny;  // det(n_k, n_l)
         const float num = (ll.qx - lk.qx) * ll.nx + (ll.qy - lk.qy) * ll.ny;
         if (fabsf(den) < 1e-4f) {
-            const double ddx = -(double)lk.ny, ddy = (double)lk.nx;
-            const double dden = ddx * (double)ll.nx + ddy * (double)ll.ny;
-            const double dnum = ((double)ll.qx - (double)lk.qx) * (double)ll.nx +
-                                ((double)ll.qy - (double)lk.qy) * (double)ll.ny;
-            if (fabs(dden) <= kEpsParallel) {
-                if (dnum > 0.0) return false;
-                continue;
-            }
-            const float t = (float)(dnum / dden);
-            if (dden > 0.0) tl = fmaxf(tl, t);
-            else tr = fminf(tr, t);
+            if (clip_near_parallel(lk, ll, tl, tr)) return false;
         } else {
-            const float t = __fdiv_rn(num, den);
+            const float t = num / den;
             if (den > 0.f) tl = fmaxf(tl, t);
             else tr = fminf(tr, t);
         }
@@ -596,19 +632,9 @@ __device__ __forceinline__ bool coop_line_interval(const Line* L, int k, float v
         const float den = dx * ll.nx + dy * ll.ny;
         const float num = (ll.qx - lk.qx) * ll.nx + (ll.qy - lk.qy) * ll.ny;
         if (fabsf(den) < 1e-4f) {
-            const double ddx = -(double)lk.ny, ddy = (double)lk.nx;
-            const double dden = ddx * (double)ll.nx + ddy * (double)ll.ny;
-            const double dnum = ((double)ll.qx - (double)lk.qx) * (double)ll.nx +
-                                ((double)ll.qy - (double)lk.qy) * (double)ll.ny;
-            if (fabs(dden) <= kEpsParallel) {
-                bad |= dnum > 0.0;
-                continue;
-            }
-            const float t = (float)(dnum / dden);
-            if (dden > 0.0) lo = fmaxf(lo, t);
-            else hi = fminf(hi, t);
+            bad |= clip_near_parallel(lk, ll, lo, hi);
         } else {
-            const float t = __fdiv_rn(num, den);
+            const float t = num / den;
             if (den > 0.f) lo = fmaxf(lo, t);
             else hi = fminf(hi, t);
         }

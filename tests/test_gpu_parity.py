@@ -43,13 +43,15 @@ def _pos_tol(scene, pos):
     return scene.dt * VEL_TOL + 4 * np.spacing(np.abs(pos).astype(np.float32)).astype(np.float64) + 1e-7
 
 
-def teacher_forced(scene, steps, sel=None, flags=0):
+def teacher_forced(scene, steps, sel=None, flags=0, tuning=None):
     """Step the GPU and the oracle from the same FP32 state for `steps` steps,
     the next state being the oracle's.  Returns the worst velocity error, the
     number of neighbour-list mismatches and the fallback count."""
     from paper_2505_00690_gb300 import crowd as cw
 
     cr = _crowd(scene, cw.CROWD_FLAG_EXPORT_NEIGHBORS | flags)
+    if tuning:
+        cr.set_tuning(**tuning)
     o = oracle.OracleScene(scene)
     S = scene.state().astype(np.float32)
     worst, mism, fb = 0.0, 0, 0
@@ -130,8 +132,7 @@ def test_dense_cluster_with_fallbacks():
 
 # ----------------------------------------------------------------------------- edge cases
 
-@pytest.mark.parametrize("sizes", [[1], [0, 5, 0], [31, 32, 33], [63, 64, 65, 1], [511, 512, 513]])
-def test_ragged_sizes(sizes):
+def _ragged_scene(sizes):
     rng = np.random.default_rng(sum(sizes))
     envs = []
     for n in sizes:
@@ -139,7 +140,12 @@ def test_ragged_sizes(sizes):
         envs.append(dict(radius=np.full(n, 0.2), max_speed=np.full(n, 1.2), pref_speed=np.full(n, 1.2),
                          pos=scenes._sample_points(rng, n, np.full(n, 0.2), 0, side, [], []),
                          vel=np.zeros((n, 2)), goal=rng.uniform(0, side, (n, 2)), segments=np.zeros((0, 4))))
-    sc = scenes._pack("ragged", envs)
+    return scenes._pack("ragged", envs)
+
+
+@pytest.mark.parametrize("sizes", [[1], [0, 5, 0], [31, 32, 33], [63, 64, 65, 1], [511, 512, 513]])
+def test_ragged_sizes(sizes):
+    sc = _ragged_scene(sizes)
     worst, mism, fb = teacher_forced(sc, 20)
     assert mism == 0 and worst <= VEL_TOL
 
@@ -374,7 +380,83 @@ def test_tuning_knobs_and_autotune():
     before = cr.state()
     t = cr.autotune(n_steps=5)
     assert t["block_threads"] in (64, 128, 256, 512) and t["cell_split"] in (1, 2)
+    assert t["lanes_per_agent"] in (1, 4, 8)
     assert np.array_equal(cr.state(), before)
     env, reach = cr.stats()
     assert all(e["steps"] == 0 for e in env) and np.all(reach == -1)
     cr.close()
+
+
+# ----------------------------------------------------------------------------- groups of lanes per agent
+
+@pytest.mark.parametrize("lanes", [2, 4, 8])
+def test_group_lanes_teacher_forced(lanes):
+    """G lanes per agent: the same contract as one thread per agent."""
+    tun = dict(block_threads=0, coop_fallback=0, cell_split=1, lanes_per_agent=lanes)
+    sc = scenes.urban_block(0, n_envs=6, steps=120)
+    worst, mism, fb = teacher_forced(sc, 120, tuning=tun)
+    assert mism == 0
+    assert worst <= VEL_TOL, worst
+    sc = scenes.uneven_batch(3, n_envs=12, steps=40)
+    worst, mism, fb = teacher_forced(sc, 40, tuning=dict(tun, cell_split=2))
+    assert mism == 0
+    assert worst <= VEL_TOL, worst
+
+
+@pytest.mark.parametrize("lanes", [2, 4, 8])
+def test_group_lanes_fallbacks_and_ragged(lanes):
+    tun = dict(block_threads=0, coop_fallback=0, cell_split=1, lanes_per_agent=lanes)
+    n = 48
+    ang = np.linspace(0, 2 * np.pi, n, endpoint=False)
+    pos = np.stack([4 * np.cos(ang), 4 * np.sin(ang)], 1)
+    sc = one_env(pos, np.zeros((n, 2)), -pos, 0.3, 1.4, segs=[(-0.5, -0.5, 0.5, 0.5)])
+    worst, mism, fb = teacher_forced(sc, 80, tuning=tun)
+    assert fb > 0 and mism == 0
+    assert worst <= VEL_TOL, worst
+    for sizes in ([1], [0, 5, 0], [63, 64, 65, 1], [511, 512, 513]):
+        sc = _ragged_scene(sizes)
+        worst, mism, fb = teacher_forced(sc, 10, tuning=tun)
+        assert mism == 0, sizes
+        assert worst <= VEL_TOL, (sizes, worst)
+
+
+def test_group_lanes_bit_identical_across_shapes():
+    """2, 4 and 8 lanes per agent, any block size and cell split: the group
+    reductions are exact (min / max) and the top-K merge is unique, so every
+    shape gives the same bits."""
+    sc = scenes.urban_block(6, n_envs=8, steps=30)
+    ref = None
+    for lanes, block, split in ((4, 0, 1), (4, 512, 2), (8, 0, 2), (8, 512, 1), (8, 256, 1), (2, 0, 1), (2, 96, 2)):
+        cr = _crowd(sc, 0)
+        cr.set_tuning(block_threads=block, coop_fallback=0, cell_split=split, lanes_per_agent=lanes)
+        assert cr.tuning()["lanes_per_agent"] == lanes
+        cr.step(sc.robot_vel[:30], n_steps=30)
+        out = cr.state()
+        cr.close()
+        if ref is None:
+            ref = out
+        assert np.array_equal(out, ref), (lanes, block, split)
+
+
+def test_group_lanes_rollout_statistics():
+    from paper_2505_00690_gb300 import crowd as cw
+
+    sc = scenes.urban_block(0, n_envs=64, steps=300)
+    steps = sc.steps
+    ref = oracle.rollout(sc, steps, threads=4)
+    cr = _crowd(sc, cw.CROWD_FLAG_STATS)
+    cr.set_tuning(block_threads=0, coop_fallback=0, cell_split=1, lanes_per_agent=4)
+    cr.step(sc.robot_vel[:steps], n_steps=steps)
+    env, reach = cr.stats()
+    ped = np.ones(sc.n_agents, bool)
+    for e in range(sc.n_envs):
+        if sc.robot_index[e] >= 0:
+            ped[sc.env_start[e] + sc.robot_index[e]] = False
+    coll = sum(s["agent_collisions"] + s["segment_collisions"] for s in env)
+    mean_speed = sum(s["speed_sum"] for s in env) / (ped.sum() * steps)
+    reached = (reach > 0) & ped
+    mrt = reach[reached].mean() * float(np.float32(sc.dt))
+    assert _close(coll, ref["collisions"], rel=0.03, floor=2 if max(coll, ref["collisions"]) < 200 else 0)
+    assert _close(mean_speed, ref["mean_speed"])
+    assert _close(mrt, ref["mean_reach_time"])
+    assert abs(reached.sum() / ped.sum() - ref["reach_fraction"]) <= max(0.01, 1.0 / ped.sum())
