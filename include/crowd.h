@@ -171,14 +171,20 @@ crowd_status crowd_read_work(crowd_t h, crowd_work* out);
  * 1e-4 m/s contract).
  *   block_threads: threads per CTA, a multiple of 32 in [32, 512], or 0 for
  *                  one thread per agent of the largest environment;
- *   coop_fallback: 1 = infeasible LPs are queued and solved by whole warps
- *                  after the pass, 0 = solved in place by their thread
- *                  (the default);
+ *   coop_fallback: 0 = infeasible LPs are solved in place by their thread
+ *                  (the default); 1 = queued and solved by whole warps after
+ *                  the pass; 2 = queued and solved after the pass by one
+ *                  thread each, spread over the warps so that no warp runs
+ *                  two of them in turn (in place when the queue is full);
  *   cell_split:    1 = grid cells >= R and a 3x3 cell search, 2 = cells
  *                  >= R/2 and a 5x5 search (fewer candidates per agent);
  *   lanes_per_agent: 1, 2, 4 or 8 lanes of a warp share each agent's work
  *                  (neighbour candidates, half-planes, LP intervals); with
- *                  more than one, fallbacks run in place; 0 means 1.
+ *                  more than one, fallbacks run in place; 0 means 1;
+ *   agent_order:   one lane per agent: 0 = each warp takes a run of agents
+ *                  in cell order, 1 = the lanes of a warp take agents
+ *                  (warps) apart in cell order, which spreads a crowded
+ *                  region over all warps.
  * block_threads 0 means one group of lanes per agent of the largest
  * environment, at most 512 threads. */
 typedef struct {
@@ -186,14 +192,15 @@ typedef struct {
     int32_t coop_fallback;
     int32_t cell_split;
     int32_t lanes_per_agent;
+    int32_t agent_order;
 } crowd_tuning;
 
 crowd_status crowd_get_tuning(crowd_t h, crowd_tuning* out);
 crowd_status crowd_set_tuning(crowd_t h, const crowd_tuning* t);
 
 /* Time every tuning candidate (one lane per agent: block_threads
- * 64/128/256/512 x coop_fallback x cell_split; 2, 4 and 8 lanes per agent: the
- * default block and 512 threads x cell_split) over n_steps steps of length dt from the current state, keep
+ * 64/128/256/512 x coop_fallback 0 and 2 x cell_split x agent_order; 2, 4 and
+ * 8 lanes per agent: the default block and 512 threads x cell_split) over n_steps steps of length dt from the current state, keep
  * the fastest, and restore the state, statistics and counters.  Waits for the
  * stream; allocates temporary device memory.  `chosen` may be NULL. */
 crowd_status crowd_autotune(crowd_t h, float dt, int32_t n_steps, crowd_tuning* chosen);
@@ -313,7 +320,7 @@ crowd_status crowd_step_noalloc(int32_t n_agents, const float* state_in, float* 
 const char* crowd_last_error(void);
 
 /* Library ABI version (increments on any signature change). */
-int32_t crowd_abi_version(void);
+int32_t crowd_abi_version(void);  /* 2 */
 
 #ifdef __cplusplus
 }

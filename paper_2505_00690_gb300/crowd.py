@@ -55,7 +55,7 @@ class crowd_work(C.Structure):
 
 class crowd_tuning(C.Structure):
     _fields_ = [("block_threads", C.c_int32), ("coop_fallback", C.c_int32), ("cell_split", C.c_int32),
-                ("lanes_per_agent", C.c_int32)]
+                ("lanes_per_agent", C.c_int32), ("agent_order", C.c_int32)]
 
 
 _lib = None
@@ -199,11 +199,11 @@ def crowd_get_tuning(h):
     t = crowd_tuning()
     _check(load().crowd_get_tuning(h, C.byref(t)))
     return dict(block_threads=t.block_threads, coop_fallback=t.coop_fallback, cell_split=t.cell_split,
-                lanes_per_agent=t.lanes_per_agent)
+                lanes_per_agent=t.lanes_per_agent, agent_order=t.agent_order)
 
 
-def crowd_set_tuning(h, block_threads=0, coop_fallback=0, cell_split=1, lanes_per_agent=1):
-    t = crowd_tuning(block_threads, coop_fallback, cell_split, lanes_per_agent)
+def crowd_set_tuning(h, block_threads=0, coop_fallback=0, cell_split=1, lanes_per_agent=1, agent_order=0):
+    t = crowd_tuning(block_threads, coop_fallback, cell_split, lanes_per_agent, agent_order)
     _check(load().crowd_set_tuning(h, C.byref(t)))
 
 
@@ -211,7 +211,7 @@ def crowd_autotune(h, dt, n_steps):
     t = crowd_tuning()
     _check(load().crowd_autotune(h, C.c_float(dt), int(n_steps), C.byref(t)))
     return dict(block_threads=t.block_threads, coop_fallback=t.coop_fallback, cell_split=t.cell_split,
-                lanes_per_agent=t.lanes_per_agent)
+                lanes_per_agent=t.lanes_per_agent, agent_order=t.agent_order)
 
 
 def crowd_reset_stats(h):

@@ -32,7 +32,8 @@ struct FbQueue {
     int* count;
     int cap, lmax;
     FbEntry* entries;
-    Line* pool;  // cap x lmax lines
+    Line* pool;      // cap x lmax lines
+    bool in_place;   // a full queue sends the agent to the in-place fallback (else it runs again)
     __device__ __forceinline__ bool push(const Line* L, int n, int n_hard, float vmax, float2 pref, int agent,
                                          float4 me) const {
         const int slot = atomicAdd(count, 1);
@@ -100,23 +101,39 @@ __device__ __forceinline__ void select_neighbors(const Src& src, int cx, int cy,
     const int ya = max(cy - span, 0), yb = min(cy + span, H - 1);
     TopK32<CAP> top;
     top.init();
-    for (int yy = ya; yy <= yb; ++yy) {
-        const int2 r = src.row(yy, xa, xb);
-        w.candidates += (unsigned long long)(r.y - r.x);
-        // the next candidate is loaded while this one is ranked
-        float4 nxt = r.x < r.y ? src.cand(r.x) : make_float4(0.f, 0.f, 0.f, 0.f);
-        for (int u = r.x; u < r.y; ++u) {
-            const float4 o = nxt;
-            if (u + 1 < r.y) nxt = src.cand(u + 1);
-            const float dx = o.x - me.x, dy = o.y - me.y;
-            const float d2 = dx * dx + dy * dy;
-            if (d2 < R2hi) {
-                if (d2 == 0.f && src.cand_id(u) == self) continue;
-                if (d2 > R2lo && !(rank_key(xi, yi, o.x, o.y) < R2bits)) continue;
-                top.insert(((unsigned long long)__float_as_uint(d2) << 32) | (unsigned)u);
-            }
+    // the rows of the cell block are walked as one sequence (a warp then
+    // iterates as often as its longest sequence, not its longest row per
+    // row), and the next candidate is loaded while this one is ranked
+    int yy = ya;
+    int2 r = src.row(yy, xa, xb);
+    unsigned long long ncand = (unsigned long long)(r.y - r.x);
+    while (r.x == r.y && yy < yb) {
+        r = src.row(++yy, xa, xb);
+        ncand += (unsigned long long)(r.y - r.x);
+    }
+    int u = r.x, end = r.y;
+    float4 nxt = u < end ? src.cand(u) : make_float4(0.f, 0.f, 0.f, 0.f);
+    while (u < end) {
+        const float4 o = nxt;
+        const int cu = u;
+        if (++u == end && yy < yb) {
+            do {
+                r = src.row(++yy, xa, xb);
+                ncand += (unsigned long long)(r.y - r.x);
+            } while (r.x == r.y && yy < yb);
+            u = r.x;
+            end = r.y;
+        }
+        if (u < end) nxt = src.cand(u);
+        const float dx = o.x - me.x, dy = o.y - me.y;
+        const float d2 = dx * dx + dy * dy;
+        if (d2 < R2hi) {
+            if (d2 == 0.f && src.cand_id(cu) == self) continue;
+            if (d2 > R2lo && !(rank_key(xi, yi, o.x, o.y) < R2bits)) continue;
+            top.insert(((unsigned long long)__float_as_uint(d2) << 32) | (unsigned)cu);
         }
     }
+    w.candidates += ncand;
     const int cnt = top.cnt;
     // tie[s]: keys s and s + 1 are near-equal (s + 1 < cnt)
     bool any_tie = false;
@@ -293,10 +310,10 @@ __device__ __forceinline__ float2 solve_velocity(const AgentParams& a, const Age
     float2 v;
     const bool feasible = lp2(L, nl, pr.y, pref, v, solves, solve_lines) == nl;
     if (!feasible) {
-        if (fbq) {
-            queued = fbq->push(L, nl, no, pr.y, pref, i, me);
-            deferred = !queued;
-        } else {
+        if (fbq) queued = fbq->push(L, nl, no, pr.y, pref, i, me);
+        if (fbq && !queued && !fbq->in_place) {
+            deferred = true;
+        } else if (!queued) {
             Line scratch[KMAX + kMaxObstacleLines];
             v = lp_fallback(L, nl, no, pr.y, pref, scratch);
         }

@@ -93,7 +93,7 @@ struct crowd_ctx {
     int res_max_agents = 0;
     int res_max_work = 0;  // largest count of solved (non-robot) agents of a resident environment
     int block = 0, grid = 0;  // resident launch shape for `tune`
-    Tuning tune{0, 0, 1, 1};
+    Tuning tune{0, 0, 1, 1, 0};
     int sms = 0;
 
     // tiled path: larger environments (or all, with CROWD_FLAG_FORCE_TILED)
@@ -364,6 +364,7 @@ crowd_status resident_steps(crowd_t h, float dt, const float2* rv, int n_steps, 
     a.cell_split = h->tune.cell_split;
     a.coop_fallback = h->tune.lanes == 1 ? h->tune.coop_fallback : 0;
     a.lanes = h->tune.lanes;
+    a.agent_order = h->tune.lanes == 1 ? h->tune.order : 0;
     CUDA_TRY(cudaMemsetAsync(h->queue, 0, sizeof(int), s), "reset work queue");
     cudaError_t e = launch_resident(a, h->grid, h->block, s);
     if (e != cudaSuccess) {
@@ -484,7 +485,7 @@ crowd_status tiled_steps(crowd_t h, float dt, const float2* rv, int n_steps, boo
 
 extern "C" {
 
-int32_t crowd_abi_version(void) { return 1; }
+int32_t crowd_abi_version(void) { return 2; }
 
 const char* crowd_last_error(void) { return g_last_error.c_str(); }
 
@@ -842,6 +843,7 @@ crowd_status crowd_get_tuning(crowd_t h, crowd_tuning* out) {
     out->coop_fallback = h->tune.coop_fallback;
     out->cell_split = h->tune.cell_split;
     out->lanes_per_agent = h->tune.lanes;
+    out->agent_order = h->tune.order;
     return CROWD_OK;
 }
 
@@ -855,7 +857,9 @@ crowd_status crowd_set_tuning(crowd_t h, const crowd_tuning* t) {
     const int lanes = t->lanes_per_agent == 0 ? 1 : t->lanes_per_agent;
     if (lanes != 1 && lanes != 2 && lanes != 4 && lanes != 8)
         return fail(CROWD_EINVAL, "lanes_per_agent must be 1, 2, 4 or 8");
-    apply_tuning(h, Tuning{t->block_threads, t->coop_fallback ? 1 : 0, t->cell_split, lanes});
+    if (t->coop_fallback < 0 || t->coop_fallback > 2) return fail(CROWD_EINVAL, "coop_fallback must be 0, 1 or 2");
+    if (t->agent_order != 0 && t->agent_order != 1) return fail(CROWD_EINVAL, "agent_order must be 0 or 1");
+    apply_tuning(h, Tuning{t->block_threads, t->coop_fallback, t->cell_split, lanes, t->agent_order});
     return CROWD_OK;
 }
 
@@ -884,18 +888,21 @@ crowd_status crowd_autotune(crowd_t h, float dt, int32_t n_steps, crowd_tuning* 
         Tuning best = before;
         float best_ms = 1e30f;
         const float tau_o = h->p.time_horizon_obst > 0.f ? h->p.time_horizon_obst : h->p.time_horizon;
-        // candidates: one lane per agent with every block size and fallback
-        // mode; groups of 4 and 8 lanes with a block of one group per agent
+        // candidates: one lane per agent with every block size, in-place or
+        // deferred one-lane fallbacks, both cell splits and both agent orders;
+        // groups of 2, 4 and 8 lanes with a block of one group per agent
         // (capped at 512 threads) or 512 threads
         std::vector<Tuning> cands;
         const int blocks[] = {64, 128, 256, 512};
         for (int bi = 0; bi < 4; ++bi)
-            for (int coop = 0; coop <= 1; ++coop)
-                for (int split = 1; split <= 2; ++split) cands.push_back(Tuning{blocks[bi], coop, split, 1});
+            for (int coop : {0, 2})
+                for (int split = 1; split <= 2; ++split)
+                    for (int order = 0; order <= 1; ++order)
+                        cands.push_back(Tuning{blocks[bi], coop, split, 1, order});
         for (int lanes : {2, 4, 8})
             for (int split = 1; split <= 2; ++split) {
-                cands.push_back(Tuning{0, 0, split, lanes});
-                cands.push_back(Tuning{512, 0, split, lanes});
+                cands.push_back(Tuning{0, 0, split, lanes, 0});
+                cands.push_back(Tuning{512, 0, split, lanes, 0});
             }
         for (size_t ci = 0; ci < cands.size() && e == cudaSuccess; ++ci) {
                 {

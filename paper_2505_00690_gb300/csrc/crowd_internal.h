@@ -78,8 +78,10 @@ struct ResidentArgs {
     int* err;               // device error word
     int max_agents;         // largest environment in `order` (sizes shared memory)
     int cell_split;         // grid cells >= R / cell_split (1: 3x3 search, 2: 5x5)
-    int coop_fallback;      // infeasible LPs solved by whole warps after the pass (1) or in place (0)
+    int coop_fallback;      // infeasible LPs: in place (0), by whole warps after the pass (1), by one
+                            // lane each after the pass, spread over the warps (2)
     int lanes;              // lanes per agent: 1, 2, 4 or 8 (groups of lanes share an agent's work)
+    int agent_order;        // one lane per agent: 0 = warps take runs of cell order, 1 = interleaved
     // Per-environment overrides (all null for a batch handle; set by the
     // serving loop, whose environments are slots of fixed capacity):
     const int* env_count;   // [E] agents, instead of env_start differences
@@ -96,6 +98,7 @@ struct Tuning {
     int coop_fallback;  // only with one lane per agent
     int cell_split;
     int lanes;          // lanes per agent: 1, 2, 4 or 8
+    int order;          // agent order over the warps (one lane per agent only)
 };
 
 // One large environment of the tiled path (static uniform grid, cell >= R).

@@ -406,7 +406,8 @@ __global__ void __launch_bounds__(kMaxThreads, G >= 4 ? 2 : 1) resident_kernel(R
         const AgentParams ap{a.R, a.dt, a.tau, a.tau_o, a.robot_alpha, a.K, a.segs, a.err};
         // the queue capacity depends on this environment alone, so that its
         // results do not depend on the batch it runs in
-        const FbQueue fbq{&s_fb_count, min(S.fb_cap, fb_capacity(c.n)), S.lmax, S.fb, S.fb_lines};
+        const FbQueue fbq{&s_fb_count, min(S.fb_cap, fb_capacity(c.n)), S.lmax, S.fb, S.fb_lines,
+                          a.coop_fallback == 2};
         const int passes = n_steps + (a.stats ? 1 : 0);
         for (int step = 0; step < passes; ++step) {
             const bool compute = step < n_steps;
@@ -432,7 +433,14 @@ __global__ void __launch_bounds__(kMaxThreads, G >= 4 ? 2 : 1) resident_kernel(R
             }
             __syncthreads();
             if (G == 1) {
-                for (int t = threadIdx.x; t < c.n; t += blockDim.x) {
+                // slot t in cell order; with agent_order 1 the lanes of a warp
+                // take slots `warps` apart, so that the agents of a crowded
+                // region (adjacent in cell order, and the costliest) are spread
+                // over all warps instead of filling one
+                const int warps = blockDim.x >> 5;
+                for (int b = 0; b < c.n; b += blockDim.x) {
+                    const int t = b + (a.agent_order ? (threadIdx.x & 31) * warps + (threadIdx.x >> 5) : threadIdx.x);
+                    if (t >= c.n) continue;
                     const bool def = agent_update<KMAX>(a, ap, S, c, t, speed_acc, tally, fbq, true);
                     S.pend[t] = def ? 1 : 0;
                     if (def) atomicAdd(&s_pend, 1);
@@ -454,9 +462,23 @@ __global__ void __launch_bounds__(kMaxThreads, G >= 4 ? 2 : 1) resident_kernel(R
                 }
             }
             __syncthreads();
+            if (a.coop_fallback == 2) {
+                // deferred fallbacks, one lane each, spread over the warps
+                // (queue entry q on warp q % warps, lane q / warps) so that no
+                // warp runs several of them one after the other
+                const int warps = blockDim.x >> 5;
+                const int q = (threadIdx.x & 31) * warps + (threadIdx.x >> 5);
+                if (q < min(s_fb_count, fbq.cap)) {
+                    const FbEntry f = S.fb[q];
+                    Line scratch[KMAX + kMaxObstacleLines];
+                    const float2 v = lp_fallback(S.fb_lines + (size_t)q * S.lmax, f.n, f.n_hard, f.vmax, f.pref, scratch);
+                    integrate(a, S, c, f.agent, f.me, S.par[f.agent].x, v, speed_acc);
+                }
+                __syncthreads();
+            }
             // cooperative fallbacks; agents that found the queue full run
             // again, round after round, until every fallback went through it
-            for (int round = 0; round <= c.n; ++round) {
+            for (int round = 0; round <= c.n && a.coop_fallback == 1; ++round) {
                 const int n_queued = min(s_fb_count, fbq.cap);
                 const int n_pend = s_pend;
                 if (n_queued) run_fallbacks(a, S, c, n_queued, speed_acc);

@@ -478,8 +478,11 @@ __device__ __forceinline__ bool line_interval(const Line* L, int k, float vmax, 
     const float sq = sqrtf(disc);
     tl = -qd - sq;
     tr = -qd + sq;
+    // the next line is loaded while this one clips
+    Line nxt = k > 0 ? L[0] : lk;
     for (int l = 0; l < k; ++l) {
-        const Line ll = L[l];
+        const Line ll = nxt;
+        if (l + 1 < k) nxt = L[l + 1];
         const float den = dx * ll.nx + dy * ll.ny;  // det(n_k, n_l)
         const float num = (ll.qx - lk.qx) * ll.nx + (ll.qy - lk.qy) * ll.ny;
         if (fabsf(den) < 1e-4f) {
@@ -522,8 +525,10 @@ __device__ __forceinline__ int lp2(const Line* L, int n, float vmax, float2 pref
     } else {
         v = pref;
     }
+    Line nxt = n > 0 ? L[0] : Line{0.f, 0.f, 0.f, 0.f};
     for (int k = 0; k < n; ++k) {
-        const Line lk = L[k];
+        const Line lk = nxt;
+        if (k + 1 < n) nxt = L[k + 1];
         if ((v.x - lk.qx) * lk.nx + (v.y - lk.qy) * lk.ny < 0.f) {
             float2 nv;
             ++solves;

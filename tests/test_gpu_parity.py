@@ -368,7 +368,7 @@ def test_tuning_knobs_and_autotune():
     # one step from a common state: in-place vs cooperative fallback
     S = ref.copy()
     outs = []
-    for coop in (0, 1):
+    for coop in (0, 1, 2):
         cr = _crowd(sc, 0)
         cr.set_tuning(block_threads=0, coop_fallback=coop, cell_split=1)
         cr.set_state(S)
@@ -376,6 +376,7 @@ def test_tuning_knobs_and_autotune():
         outs.append(cr.state())
         cr.close()
     assert np.abs(outs[0] - outs[1]).max() <= VEL_TOL
+    assert np.abs(outs[0] - outs[2]).max() <= VEL_TOL
     cr = _crowd(sc, cw.CROWD_FLAG_STATS)
     before = cr.state()
     t = cr.autotune(n_steps=5)
@@ -460,3 +461,41 @@ def test_group_lanes_rollout_statistics():
     assert _close(mean_speed, ref["mean_speed"])
     assert _close(mrt, ref["mean_reach_time"])
     assert abs(reached.sum() / ped.sum() - ref["reach_fraction"]) <= max(0.01, 1.0 / ped.sum())
+
+
+@pytest.mark.parametrize("coop", [1, 2])
+def test_deferred_fallback_modes_teacher_forced(coop):
+    """Fallbacks queued after the pass (whole warps, or one lane each spread
+    over the warps): the same contract as in-place fallbacks, on a jammed ring
+    and on urban blocks."""
+    tun = dict(block_threads=0, coop_fallback=coop, cell_split=1, lanes_per_agent=1)
+    n = 48
+    ang = np.linspace(0, 2 * np.pi, n, endpoint=False)
+    pos = np.stack([4 * np.cos(ang), 4 * np.sin(ang)], 1)
+    sc = one_env(pos, np.zeros((n, 2)), -pos, 0.3, 1.4, segs=[(-0.5, -0.5, 0.5, 0.5)])
+    worst, mism, fb = teacher_forced(sc, 80, tuning=tun)
+    assert fb > 0 and mism == 0
+    assert worst <= VEL_TOL, worst
+    sc = scenes.urban_block(1, n_envs=6, steps=60)
+    worst, mism, fb = teacher_forced(sc, 60, tuning=tun)
+    assert mism == 0
+    assert worst <= VEL_TOL, worst
+
+
+def test_agent_order_and_deferred_fallback_change_no_bit():
+    """In-place and deferred one-lane fallbacks run the same arithmetic on the
+    same lines, and the agent order only changes which thread computes an
+    agent: every combination gives the same bits."""
+    sc = scenes.urban_block(2, n_envs=8, steps=40)
+    ref = None
+    for block, coop, order, split in ((0, 0, 0, 1), (0, 2, 0, 1), (0, 0, 1, 1), (0, 2, 1, 2), (256, 2, 1, 1),
+                                      (64, 0, 1, 2), (512, 2, 0, 1)):
+        cr = _crowd(sc, 0)
+        cr.set_tuning(block_threads=block, coop_fallback=coop, cell_split=split, agent_order=order)
+        assert cr.tuning()["agent_order"] == order
+        cr.step(sc.robot_vel[:40], n_steps=40)
+        out = cr.state()
+        cr.close()
+        if ref is None:
+            ref = out
+        assert np.array_equal(out, ref), (block, coop, order, split)
