@@ -42,10 +42,9 @@ N_SMS = 152
 
 
 def _dist_env():
-    ws = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return ws, rank, local
+    from paper_2505_00690_gb300 import replicas
+
+    return replicas.dist_env()
 
 
 class Clocks:
@@ -124,6 +123,7 @@ def run_ours(args):
     import torch
 
     from paper_2505_00690_gb300 import crowd as cw
+    from paper_2505_00690_gb300 import replicas
     from paper_2505_00690_gb300 import scenes
 
     ws, rank, local = _dist_env()
@@ -139,7 +139,7 @@ def run_ours(args):
     from paper_2505_00690_gb300 import build as B
 
     B.build()
-    sc = scenes.urban_block(seed=rank, steps=ROLLOUT)
+    sc = scenes.urban_block(seed=replicas.replica_seed(rank), steps=ROLLOUT)
     n_agents = sc.n_agents
     with torch.cuda.stream(stream):
         cr = cw.Crowd(sc, flags=0, stream=stream.cuda_stream)
@@ -181,14 +181,13 @@ def run_ours(args):
     if dist:
         tdist.barrier()
     per = [s.elapsed_time(e) for s, e in zip(starts, ends)]  # ms
-    dev_ms = float(sum(per))
-    if dist:
-        t = torch.tensor([dev_ms], device=dev)
-        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
-        dev_ms = float(t.item())
+    my_ms = float(sum(per))
     clocks = clk.summary()
-    total_agent_steps = n_agents * ROLLOUT * args.steps * ws
-    value = total_agent_steps / (dev_ms / 1e3)
+    # replicas: this rank's agent-steps, the slowest rank's time
+    my_agent_steps = n_agents * ROLLOUT * args.steps
+    value = replicas.aggregate_throughput(my_agent_steps, my_ms / 1e3, device=dev)
+    total_agent_steps = replicas.sum_over_ranks(my_agent_steps, device=dev)
+    dev_ms = replicas.max_over_ranks(my_ms, device=dev)
 
     # ---- e2e: same rollouts through the C ABI with pinned host buffers
     init_h = torch.from_numpy(sc.state()).pin_memory()
@@ -210,11 +209,7 @@ def run_ours(args):
     for _ in range(args.steps):
         e2e_step()
     torch.cuda.synchronize(dev)
-    e2e_s = time.perf_counter() - t0
-    if dist:
-        t = torch.tensor([e2e_s], device=dev)
-        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = replicas.max_over_ranks(time.perf_counter() - t0, device=dev)
     e2e = {"value": total_agent_steps / e2e_s, "unit": UNIT,
            "h2d_bytes_per_step": int(init_h.numel() * 4 + rv_h.numel() * 4),
            "d2h_bytes_per_step": int(out_h.numel() * 4)}
@@ -363,9 +358,11 @@ def run_reference(args):
 
 
 def profile_case(which):
-    """Small launches for ncu captures: `resident` = one 20-step launch of the
-    256-env urban block (after one warm launch); `tiled` = two single steps of
-    one 20,000-agent dense-crowd environment (the second is captured)."""
+    """Launches for ncu captures: `resident` = one 20-step launch of the
+    256-env urban block (after one warm launch); `rollout` = the same with the
+    full 1000-step rollout (for one-pass counters only); `tiled` = two single
+    steps of one 20,000-agent dense-crowd environment (the second is
+    captured)."""
     from paper_2505_00690_gb300 import build as B
     from paper_2505_00690_gb300 import crowd as cw
     from paper_2505_00690_gb300 import scenes
@@ -377,6 +374,14 @@ def profile_case(which):
         cr.step(sc.robot_vel[:20], n_steps=20)
         cr.set_state(sc.state())
         cr.step(sc.robot_vel[:20], n_steps=20)
+    elif which == "rollout":
+        # the timed launch of the default run: one 1000-step rollout of the
+        # 256-env urban block (default launch shape), after a warm one
+        sc = scenes.urban_block(0, steps=ROLLOUT)
+        cr = cw.Crowd(sc)
+        cr.step(sc.robot_vel[:ROLLOUT], n_steps=ROLLOUT)
+        cr.set_state(sc.state())
+        cr.step(sc.robot_vel[:ROLLOUT], n_steps=ROLLOUT)
     else:
         sc = scenes.dense_crowd(0, n_envs=1, steps=4)
         cr = cw.Crowd(sc)
@@ -399,7 +404,7 @@ def main():
     ap.add_argument("--serve", action="store_true",
                     help="also replay the serving workload (Poisson request stream) and report p50/p99 latency")
     ap.add_argument("--serve-seconds", type=float, default=10.0)
-    ap.add_argument("--profile-case", choices=["resident", "tiled"], default=None,
+    ap.add_argument("--profile-case", choices=["resident", "rollout", "tiled"], default=None,
                     help="run a small case for an ncu capture and exit")
     args = ap.parse_args()
     if args.profile_case:
