@@ -322,6 +322,39 @@ def cpu_baseline(sc, budget_s=12.0, threads=None):
             "sample": f"{steps} consecutive steps of all {sc.n_envs} envs ({sc.n_agents} agents), FP64, OpenMP over agents"}
 
 
+def cpu_table(budget_s=6.0):
+    """The FP64 oracle as it stands on each workload of the benchmark table,
+    one thread and all host threads, on bounded samples (consecutive steps
+    of the whole batch, or of its first environments where one step of the
+    whole batch takes longer than the budget).  One JSON line per workload."""
+    import oracle
+    from paper_2505_00690_gb300 import scenes
+
+    cores = os.cpu_count() or 1
+    cases = [("plain_square", scenes.plain_square(0), None), ("urban_block", scenes.urban_block(0), None),
+             ("uneven_batch", scenes.uneven_batch(0), None),
+             ("dense_crowd", scenes.dense_crowd(0), 1)]  # one 20,000-agent env of the 16
+    for name, sc, n_env in cases:
+        if n_env is not None:
+            sc = sc.subset(list(range(n_env)))
+        o = oracle.OracleScene(sc)
+        res = {}
+        for threads in (1, cores):
+            pos, vel = sc.pos.astype(np.float64), sc.vel.astype(np.float64)
+            steps = 0
+            t0 = time.perf_counter()
+            while True:
+                rv = sc.robot_vel_at(steps) if sc.robot_vel is not None else None
+                pos, vel, _, _ = o.step(pos, vel, rv, threads=threads)
+                steps += 1
+                if time.perf_counter() - t0 >= budget_s or steps >= sc.steps:
+                    break
+            dt = time.perf_counter() - t0
+            res[threads] = {"value": sc.n_agents * steps / dt, "steps": steps}
+        print(json.dumps({"workload": name, "unit": UNIT, "kind": "oracle", "agents_in_sample": sc.n_agents,
+                          "one_core": res[1], "all_cores": res[cores], "cores": cores}), flush=True)
+
+
 def run_reference(args):
     ws, rank, local = _dist_env()
     if rank != 0:
@@ -406,10 +439,14 @@ def main():
     ap.add_argument("--serve", action="store_true",
                     help="also replay the serving workload (Poisson request stream) and report p50/p99 latency")
     ap.add_argument("--serve-seconds", type=float, default=10.0)
+    ap.add_argument("--cpu-table", action="store_true",
+                    help="time the FP64 oracle on every workload (1 and all host threads) and exit")
     ap.add_argument("--profile-case", choices=["resident", "rollout", "tiled"], default=None,
                     help="run a small case for an ncu capture and exit")
     args = ap.parse_args()
-    if args.profile_case:
+    if args.cpu_table:
+        cpu_table()
+    elif args.profile_case:
         profile_case(args.profile_case)
     elif args.impl == "reference":
         run_reference(args)
