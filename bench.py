@@ -37,6 +37,10 @@ METRIC = "agent-steps/sec at <=1e-4 m/s vs FP64 oracle, batched vs plain; p50/p9
 UNIT = "agent-steps/s"
 WORKLOAD = "urban_block: 256 envs x (128 peds + 1 robot), 40x40 m, 36 segments/env, 1000-step rollout, dt 0.1"
 ROLLOUT = 1000
+# dram__bytes_read.sum + dram__bytes_write.sum of one 1000-step rollout launch of
+# the resident kernel (ncu, `bench.py --profile-case rollout`, one pass); taken
+# again whenever the kernel changes
+ROLLOUT_DRAM_BYTES = 13.43e6
 FP32_LANES_PER_SM = 128
 N_SMS = 152
 
@@ -228,7 +232,7 @@ def run_ours(args):
     fp32_peak = N_SMS * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12  # TFLOP/s
     achieved = flops / launch_s / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
-                "frac": achieved / fp32_peak, "traffic": None,
+                "frac": achieved / fp32_peak, "traffic": ROLLOUT_DRAM_BYTES,
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz max SM clock",
                 "flops_per_launch": flops, "work_per_agent_step": {k: v / max(1, work["agent_steps"])
                                                                    for k, v in work.items() if k != "agent_steps"}}
