@@ -152,10 +152,10 @@ def run_ours(args):
         flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
     torch.cuda.synchronize(dev)
 
-    # launch shape chosen by the library's autotuner (untimed): 400 steps from
-    # the start state, long enough for the crowded regions that set the
-    # rollout time to form
-    tuning = cr.autotune(n_steps=400)
+    # launch shape chosen by the library's autotuner (untimed), each candidate
+    # timed on a whole rollout: the crowded regions that set the rollout time
+    # form over hundreds of steps
+    tuning = cr.autotune(n_steps=ROLLOUT)
 
     def one_rollout():
         cr.step(rv_dev, n_steps=ROLLOUT)

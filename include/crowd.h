@@ -176,8 +176,8 @@ crowd_status crowd_read_work(crowd_t h, crowd_work* out);
  *                  the pass; 2 = queued and solved after the pass by one
  *                  thread each, spread over the warps so that no warp runs
  *                  two of them in turn (in place when the queue is full);
- *   cell_split:    1 = grid cells >= R and a 3x3 cell search, 2 = cells
- *                  >= R/2 and a 5x5 search (fewer candidates per agent);
+ *   cell_split:    s = 1, 2 or 3: grid cells >= R/s and a (2s+1)^2 cell
+ *                  search (finer cells, fewer candidates per agent);
  *   lanes_per_agent: 1, 2, 4 or 8 lanes of a warp share each agent's work
  *                  (neighbour candidates, half-planes, LP intervals); with
  *                  more than one, fallbacks run in place; 0 means 1;
@@ -199,8 +199,9 @@ crowd_status crowd_get_tuning(crowd_t h, crowd_tuning* out);
 crowd_status crowd_set_tuning(crowd_t h, const crowd_tuning* t);
 
 /* Time every tuning candidate (one lane per agent: block_threads
- * 64/128/256/512 x coop_fallback 0 and 2 x cell_split x agent_order; 2, 4 and
- * 8 lanes per agent: the default block and 512 threads x cell_split) over n_steps steps of length dt from the current state, keep
+ * default/64/128/256/512 x coop_fallback 0 and 2 x cell_split 1-3 x
+ * agent_order; 2, 4 and 8 lanes per agent: the default block and 512 threads
+ * x cell_split 1-2) over n_steps steps of length dt from the current state, keep
  * the fastest, and restore the state, statistics and counters.  Waits for the
  * stream; allocates temporary device memory.  `chosen` may be NULL. */
 crowd_status crowd_autotune(crowd_t h, float dt, int32_t n_steps, crowd_tuning* chosen);

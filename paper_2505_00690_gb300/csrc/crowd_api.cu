@@ -853,7 +853,7 @@ crowd_status crowd_set_tuning(crowd_t h, const crowd_tuning* t) {
     if (!t) return fail(CROWD_EINVAL, "tuning is null");
     if (t->block_threads != 0 && (t->block_threads < 32 || t->block_threads > 512 || t->block_threads % 32))
         return fail(CROWD_EINVAL, "block_threads must be 0 or a multiple of 32 in [32, 512]");
-    if (t->cell_split != 1 && t->cell_split != 2) return fail(CROWD_EINVAL, "cell_split must be 1 or 2");
+    if (t->cell_split < 1 || t->cell_split > 3) return fail(CROWD_EINVAL, "cell_split must be 1, 2 or 3");
     const int lanes = t->lanes_per_agent == 0 ? 1 : t->lanes_per_agent;
     if (lanes != 1 && lanes != 2 && lanes != 4 && lanes != 8)
         return fail(CROWD_EINVAL, "lanes_per_agent must be 1, 2, 4 or 8");
@@ -893,10 +893,10 @@ crowd_status crowd_autotune(crowd_t h, float dt, int32_t n_steps, crowd_tuning* 
         // groups of 2, 4 and 8 lanes with a block of one group per agent
         // (capped at 512 threads) or 512 threads
         std::vector<Tuning> cands;
-        const int blocks[] = {64, 128, 256, 512};
-        for (int bi = 0; bi < 4; ++bi)
+        const int blocks[] = {0, 64, 128, 256, 512};
+        for (int bi = 0; bi < 5; ++bi)
             for (int coop : {0, 2})
-                for (int split = 1; split <= 2; ++split)
+                for (int split = 1; split <= 3; ++split)
                     for (int order = 0; order <= 1; ++order)
                         cands.push_back(Tuning{blocks[bi], coop, split, 1, order});
         for (int lanes : {2, 4, 8})
