@@ -137,8 +137,28 @@ crowd_status crowd_create(int32_t n_envs, const int32_t* agents_per_env, const f
                           const int32_t* robot_index, const int32_t* segs_per_env, const float* segments,
                           const crowd_params* p, void* cuda_stream, crowd_t* out);
 
-/* Goals [N][2]. */
+/* Goals [N][2] (fixed goals; removes a goal queue). */
 crowd_status crowd_set_goals(crowd_t h, const float* goals, int32_t ptr_kind);
+
+/* Goal queues (continuing walks after arrival; the paper's agents walk
+ * between sampled start and end points, Sec. 3.2, and the simulation runs on
+ * past their arrival).  Agent i walks to goals[i][0], then goals[i][1], ...:
+ * at the start of every step, an agent (not the robot) whose position p lies
+ * within its radius r of its current goal g, |g - p|^2 <= r^2 (decided as an
+ * FP64 evaluation of the FP32 values decides it), moves on to its next goal,
+ * which it steers to from that step on.  After the last goal the queue starts
+ * again when `cyclic` != 0; otherwise the agent keeps its last goal.
+ *   n_goals: goals per agent, 1..CROWD_MAX_GOALS; goals [N][n_goals][2],
+ *            host or device (copied).
+ * The first goal of each queue becomes the agent's current goal and every
+ * counter is reset to 0; crowd_set_goals removes the queue.  Waits for the
+ * handle's stream; allocates device memory on the first call. */
+#define CROWD_MAX_GOALS 64
+crowd_status crowd_set_goal_queue(crowd_t h, int32_t n_goals, const float* goals, int32_t cyclic, int32_t ptr_kind);
+
+/* Host copy [N] of how many goals each agent has moved past since its queue
+ * was set (0 without a queue).  Waits. */
+crowd_status crowd_read_goal_index(crowd_t h, int32_t* out);
 
 /* Full state [N][4] (px, py, vx, vy): resume from a checkpoint, or teacher
  * forcing from another simulator's state. */

@@ -102,6 +102,34 @@ def pref_velocity(p, g, speed, dt):
     return np.array([vx.value, vy.value])
 
 
+def advance_goals(pos, radius, goal, idx, queue, cyclic, skip=None):
+    """Goal queues (a reading: the paper's agents walk between sampled start
+    and end points, Sec. 3.2, and the simulation runs on past an arrival).
+
+    At the start of a step, every agent (rows of `skip` excepted: the robot)
+    whose position p lies within its radius r of its current goal g,
+    (gx - px)^2 + (gy - py)^2 <= r^2 in FP64 with each operation rounded once,
+    moves on to the next goal of its queue: queue[i][idx + 1], wrapping to
+    the start when `cyclic`, else staying at the last goal.  Returns the new
+    (goal [N][2], idx [N]); the inputs are not modified."""
+    p = np.asarray(pos, np.float64).reshape(-1, 2)
+    g = np.array(goal, np.float64).reshape(-1, 2)
+    k = np.array(idx, np.int64).reshape(-1)
+    qu = np.asarray(queue, np.float64)
+    n_goals = qu.shape[1]
+    r = np.asarray(radius, np.float64).reshape(-1)
+    dx = g[:, 0] - p[:, 0]
+    dy = g[:, 1] - p[:, 1]
+    reached = dx * dx + dy * dy <= r * r
+    if skip is not None:
+        reached &= ~np.asarray(skip, bool)
+    move = reached & (bool(cyclic) | (k + 1 < n_goals))
+    k[move] += 1
+    rows = np.nonzero(move)[0]
+    g[rows] = qu[rows, k[rows] % n_goals]
+    return g, k
+
+
 def rank_key(pi, pj):
     """O2 ranking key (FP64 squared distance, no FMA)."""
     return lib().or_rank_key(float(pi[0]), float(pi[1]), float(pj[0]), float(pj[1]))

@@ -28,7 +28,8 @@ STATUS_NAMES = {0: "CROWD_OK", 1: "CROWD_EINVAL", 2: "CROWD_ENOMEM", 3: "CROWD_E
 EXPORTED = ["crowd_create", "crowd_set_goals", "crowd_set_state", "crowd_step", "crowd_read_state",
             "crowd_read_neighbors", "crowd_read_stats", "crowd_read_work", "crowd_reset_stats", "crowd_synchronize",
             "crowd_destroy", "crowd_num_agents", "crowd_num_envs", "crowd_last_error", "crowd_abi_version",
-            "crowd_get_tuning", "crowd_set_tuning", "crowd_autotune"]
+            "crowd_get_tuning", "crowd_set_tuning", "crowd_autotune", "crowd_set_goal_queue",
+            "crowd_read_goal_index"]
 
 
 class CrowdError(RuntimeError):
@@ -72,6 +73,8 @@ def load(path: str = LIB_PATH):
     vp, fp, ip, i32 = C.c_void_p, C.POINTER(C.c_float), C.POINTER(C.c_int32), C.c_int32
     L.crowd_create.argtypes = [i32, vp, vp, vp, vp, vp, vp, vp, vp, C.POINTER(crowd_params), vp, C.POINTER(vp)]
     L.crowd_set_goals.argtypes = [vp, vp, i32]
+    L.crowd_set_goal_queue.argtypes = [vp, i32, vp, i32, i32]
+    L.crowd_read_goal_index.argtypes = [vp, vp]
     L.crowd_set_state.argtypes = [vp, vp, i32]
     L.crowd_step.argtypes = [vp, C.c_float, vp, i32, i32]
     L.crowd_read_state.argtypes = [vp, vp, i32]
@@ -259,6 +262,17 @@ class Crowd:
 
     def set_goals(self, goals):
         crowd_set_goals(self.h, goals)
+
+    def set_goal_queue(self, queue, cyclic=True):
+        """queue [N][Q][2]: each agent's goals in order (see crowd_set_goal_queue)."""
+        q = np.ascontiguousarray(queue, np.float32)
+        assert q.ndim == 3 and q.shape[0] == self.N and q.shape[2] == 2
+        _check(load().crowd_set_goal_queue(self.h, int(q.shape[1]), q.ctypes.data, int(bool(cyclic)), CROWD_HOST))
+
+    def goal_index(self):
+        out = np.zeros(self.N, np.int32)
+        _check(load().crowd_read_goal_index(self.h, out.ctypes.data))
+        return out
 
     def step(self, robot_vel=None, n_steps=1, dt=None):
         crowd_step(self.h, self.scene.dt if dt is None else dt, robot_vel, n_steps)

@@ -45,6 +45,30 @@ struct FbQueue {
     }
 };
 
+// Goal queues: agent g walks to queue[g][0], queue[g][1], ... and moves on to
+// its next goal at the start of a step in which its position lies within its
+// radius of the current goal, (g - p)^2 <= r^2, decided exactly as an FP64
+// evaluation of the FP32 inputs decides it (exact differences and squares,
+// one rounding of the sum): FP32 settles it unless d^2 is within 1e-5 of r^2
+// relative, where the FP32 error (< 1e-6 relative) could flip it.
+__device__ __forceinline__ bool goal_reached(float px, float py, float gx, float gy, float r) {
+    const float dx = gx - px, dy = gy - py;
+    const float d2 = dx * dx + dy * dy, r2 = r * r;
+    if (fabsf(d2 - r2) > 1e-5f * r2) return d2 < r2;
+    const double ex = __dsub_rn((double)gx, (double)px), ey = __dsub_rn((double)gy, (double)py);
+    const double dr = (double)r;
+    return __dadd_rn(__dmul_rn(ex, ex), __dmul_rn(ey, ey)) <= __dmul_rn(dr, dr);
+}
+
+// Advance agent g (global index) past a reached goal; returns its goal.
+__device__ __forceinline__ float2 advance_goal(const GoalQueue& gq, int g, float4 p, float r, float2 cur) {
+    if (gq.q <= 0 || !goal_reached(p.x, p.y, cur.x, cur.y, r)) return cur;
+    const int k = gq.idx[g];
+    if (!gq.cyclic && k + 1 >= gq.q) return cur;  // stays at its last goal
+    gq.idx[g] = k + 1;
+    return gq.queue[(size_t)g * gq.q + (gq.cyclic ? (k + 1) % gq.q : k + 1)];
+}
+
 // Per-thread work tallies (only reported when counting is on).
 struct Tally {
     unsigned long long agent_steps = 0, candidates = 0, agent_lines = 0, obstacle_lines = 0, segment_tests = 0,

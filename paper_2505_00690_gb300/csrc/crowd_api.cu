@@ -80,6 +80,10 @@ struct crowd_ctx {
     float4* state = nullptr;
     float4* par = nullptr;
     float2* goal = nullptr;
+    float2* goal_queue = nullptr;  // [N][goal_q] (crowd_set_goal_queue)
+    int* goal_idx = nullptr;       // [N]
+    int goal_q = 0, goal_cyclic = 0;
+    size_t goal_queue_cap = 0;     // entries allocated in goal_queue
     float4* segs = nullptr;
     float2* robot_vel = nullptr;
     size_t robot_vel_cap = 0;
@@ -123,7 +127,7 @@ struct crowd_ctx {
     ~crowd_ctx() {
         if (graph) cudaGraphExecDestroy(graph);
         if (cap_stream) cudaStreamDestroy(cap_stream);
-        void* ptrs[] = {env_start, seg_start, robot_index, order, queue, err, state, par, goal,
+        void* ptrs[] = {env_start, seg_start, robot_index, order, queue, err, state, par, goal, goal_queue, goal_idx,
                         segs, robot_vel, nbr, reach, stats, work, tenvs, state_b, sorted_pv, key, rank,
                         count, start, sorted_id, seg_cell_start, seg_cell_ids, seg_grid, d_step};
         for (void* q : ptrs)
@@ -229,6 +233,14 @@ SegGrid build_seg_grid(int base, int n, int seg0, int ns, const float* radii, co
 }  // namespace crowd
 
 namespace {
+
+// Cached tiled graphs bake the kernel arguments in, goal queue included.
+void drop_graph(crowd_t h) {
+    if (h->graph) {
+        cudaGraphExecDestroy(h->graph);
+        h->graph = nullptr;
+    }
+}
 
 crowd_status check_handle(crowd_t h) {
     if (!h) return fail(CROWD_EINVAL, "null handle");
@@ -344,6 +356,7 @@ crowd_status resident_steps(crowd_t h, float dt, const float2* rv, int n_steps, 
     a.seg_cell_ids = h->seg_cell_ids;
     a.par = h->par;
     a.goal = h->goal;
+    a.goals = GoalQueue{h->goal_queue, h->goal_idx, h->goal_q, h->goal_cyclic};
     a.state = h->state;
     a.robot_vel = rv;
     a.robot_stride = h->E;
@@ -385,6 +398,7 @@ TiledStepArgs tiled_args(crowd_t h, float dt, const float2* rv, int s, int n_ste
     a.robot_vel = (rv && mode != kTiledStatsOnly) ? rv + (size_t)s * h->E : nullptr;
     a.par = h->par;
     a.goal = h->goal;
+    a.goals = GoalQueue{h->goal_queue, h->goal_idx, h->goal_q, h->goal_cyclic};
     a.segs = h->segs;
     a.seg_cell_start = h->seg_cell_start;
     a.seg_cell_ids = h->seg_cell_ids;
@@ -723,7 +737,59 @@ crowd_status crowd_set_goals(crowd_t h, const float* goals, int32_t ptr_kind) {
     if (h->N == 0) return CROWD_OK;
     if (!goals) return fail(CROWD_EINVAL, "goals is null");
     if (ptr_kind == CROWD_HOST && !finite_all(goals, (size_t)h->N * 2)) return fail(CROWD_EINVAL, "goals hold NaN/Inf");
+    if (h->goal_q) {
+        h->goal_q = 0;  // fixed goals replace a goal queue
+        drop_graph(h);
+    }
     return copy_in(h, h->goal, goals, sizeof(float2) * h->N, ptr_kind, "copy goals");
+}
+
+crowd_status crowd_set_goal_queue(crowd_t h, int32_t n_goals, const float* goals, int32_t cyclic, int32_t ptr_kind) {
+    crowd_status st = check_handle(h);
+    if (st) return st;
+    if (n_goals < 1 || n_goals > CROWD_MAX_GOALS) return fail(CROWD_EINVAL, "n_goals must be in [1, %d]", CROWD_MAX_GOALS);
+    if (ptr_kind != CROWD_HOST && ptr_kind != CROWD_DEVICE) return fail(CROWD_EINVAL, "ptr_kind must be 0 or 1");
+    if (h->N == 0) return CROWD_OK;
+    if (!goals) return fail(CROWD_EINVAL, "goals is null");
+    const size_t count = (size_t)h->N * n_goals;
+    if (ptr_kind == CROWD_HOST && !finite_all(goals, count * 2)) return fail(CROWD_EINVAL, "goals hold NaN/Inf");
+    CUDA_TRY(cudaStreamSynchronize(h->stream), "synchronize");
+    if (h->goal_queue && h->goal_queue_cap < count) {
+        cudaFree(h->goal_queue);
+        h->goal_queue = nullptr;
+        h->goal_queue_cap = 0;
+    }
+    if (!h->goal_queue) {
+        CUDA_TRY(dev_alloc(&h->goal_queue, count), "allocate goal queue");
+        h->goal_queue_cap = count;
+    }
+    if (!h->goal_idx) CUDA_TRY(dev_alloc(&h->goal_idx, (size_t)h->N), "allocate goal counters");
+    h->goal_q = 0;  // until the copies below succeed
+    st = copy_in(h, h->goal_queue, goals, sizeof(float2) * count, ptr_kind, "copy goal queue");
+    if (st) return st;
+    CUDA_TRY(cudaMemsetAsync(h->goal_idx, 0, sizeof(int) * h->N, h->stream), "clear goal counters");
+    // the current goal of every agent becomes the first of its queue
+    CUDA_TRY(cudaMemcpy2DAsync(h->goal, sizeof(float2), h->goal_queue, sizeof(float2) * n_goals, sizeof(float2),
+                               (size_t)h->N, cudaMemcpyDeviceToDevice, h->stream),
+             "set first goals");
+    h->goal_q = n_goals;
+    h->goal_cyclic = cyclic ? 1 : 0;
+    drop_graph(h);
+    return CROWD_OK;
+}
+
+crowd_status crowd_read_goal_index(crowd_t h, int32_t* out) {
+    crowd_status st = check_handle(h);
+    if (st) return st;
+    if (!out) return fail(CROWD_EINVAL, "out is null");
+    if (h->N == 0) return CROWD_OK;
+    if (!h->goal_idx || h->goal_q == 0) {
+        std::fill(out, out + h->N, 0);
+        return CROWD_OK;
+    }
+    CUDA_TRY(cudaMemcpyAsync(out, h->goal_idx, sizeof(int) * h->N, cudaMemcpyDeviceToHost, h->stream), "copy goal counters");
+    CUDA_TRY(cudaStreamSynchronize(h->stream), "synchronize");
+    return CROWD_OK;
 }
 
 crowd_status crowd_set_state(crowd_t h, const float* state, int32_t ptr_kind) {
@@ -872,10 +938,26 @@ crowd_status crowd_autotune(crowd_t h, float dt, int32_t n_steps, crowd_tuning* 
         float4* saved = nullptr;
         EnvStats* saved_stats = nullptr;
         int* saved_reach = nullptr;
+        float2* saved_goal = nullptr;  // with a goal queue, trials move goals on
+        int* saved_gidx = nullptr;
         WorkCount saved_work{};
         CUDA_TRY(dev_alloc(&saved, h->N), "autotune scratch");
         cudaError_t e = dev_alloc(&saved_stats, h->E);
         if (e == cudaSuccess) e = dev_alloc(&saved_reach, h->N);
+        if (e == cudaSuccess && h->goal_q) e = dev_alloc(&saved_goal, h->N);
+        if (e == cudaSuccess && h->goal_q) e = dev_alloc(&saved_gidx, h->N);
+        if (e == cudaSuccess && h->goal_q)
+            e = cudaMemcpyAsync(saved_goal, h->goal, sizeof(float2) * h->N, cudaMemcpyDeviceToDevice, h->stream);
+        if (e == cudaSuccess && h->goal_q)
+            e = cudaMemcpyAsync(saved_gidx, h->goal_idx, sizeof(int) * h->N, cudaMemcpyDeviceToDevice, h->stream);
+        auto restore_start = [&]() {
+            cudaError_t r = cudaMemcpyAsync(h->state, saved, sizeof(float4) * h->N, cudaMemcpyDeviceToDevice, h->stream);
+            if (r == cudaSuccess && h->goal_q)
+                r = cudaMemcpyAsync(h->goal, saved_goal, sizeof(float2) * h->N, cudaMemcpyDeviceToDevice, h->stream);
+            if (r == cudaSuccess && h->goal_q)
+                r = cudaMemcpyAsync(h->goal_idx, saved_gidx, sizeof(int) * h->N, cudaMemcpyDeviceToDevice, h->stream);
+            return r;
+        };
         cudaEvent_t t0 = nullptr, t1 = nullptr;
         if (e == cudaSuccess) e = cudaEventCreate(&t0);
         if (e == cudaSuccess) e = cudaEventCreate(&t1);
@@ -889,7 +971,7 @@ crowd_status crowd_autotune(crowd_t h, float dt, int32_t n_steps, crowd_tuning* 
         float best_ms = 1e30f;
         const float tau_o = h->p.time_horizon_obst > 0.f ? h->p.time_horizon_obst : h->p.time_horizon;
         // candidates: one lane per agent with every block size, in-place or
-        // deferred one-lane fallbacks, both cell splits and both agent orders;
+        // deferred one-lane fallbacks, cell splits 1-3 and both agent orders;
         // groups of 2, 4 and 8 lanes with a block of one group per agent
         // (capped at 512 threads) or 512 threads
         std::vector<Tuning> cands;
@@ -909,7 +991,7 @@ crowd_status crowd_autotune(crowd_t h, float dt, int32_t n_steps, crowd_tuning* 
                     apply_tuning(h, cands[ci]);
                     float ms = 0.f;
                     for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {
-                        e = cudaMemcpyAsync(h->state, saved, sizeof(float4) * h->N, cudaMemcpyDeviceToDevice, h->stream);
+                        e = restore_start();
                         if (e != cudaSuccess) break;
                         if (rep == 1) e = cudaEventRecord(t0, h->stream);
                         if (e != cudaSuccess) break;
@@ -929,7 +1011,7 @@ crowd_status crowd_autotune(crowd_t h, float dt, int32_t n_steps, crowd_tuning* 
                     }
                 }
         }
-        if (e == cudaSuccess) e = cudaMemcpyAsync(h->state, saved, sizeof(float4) * h->N, cudaMemcpyDeviceToDevice, h->stream);
+        if (e == cudaSuccess) e = restore_start();
         if (e == cudaSuccess) e = cudaMemcpyAsync(h->stats, saved_stats, sizeof(EnvStats) * h->E, cudaMemcpyDeviceToDevice, h->stream);
         if (e == cudaSuccess) e = cudaMemcpyAsync(h->reach, saved_reach, sizeof(int) * h->N, cudaMemcpyDeviceToDevice, h->stream);
         if (e == cudaSuccess && h->work)
@@ -940,6 +1022,8 @@ crowd_status crowd_autotune(crowd_t h, float dt, int32_t n_steps, crowd_tuning* 
         cudaFree(saved);
         if (saved_stats) cudaFree(saved_stats);
         if (saved_reach) cudaFree(saved_reach);
+        if (saved_goal) cudaFree(saved_goal);
+        if (saved_gidx) cudaFree(saved_gidx);
         apply_tuning(h, e == cudaSuccess ? best : before);
         if (e != cudaSuccess) return cuda_fail(e, "autotune");
     }

@@ -7,6 +7,14 @@
 
 namespace crowd {
 
+// Goal queue of a handle (see crowd_set_goal_queue).
+struct GoalQueue {
+    const float2* queue;  // [N][q]
+    int* idx;             // [N] goals reached since the queue was set
+    int q;                // goals per agent (0: no queue)
+    int cyclic;           // 1: after the last goal the queue starts again
+};
+
 // Device error word bits.
 enum : int {
     kErrObstacleOverflow = 1,  // an agent had more segments in reach than the line buffer holds
@@ -63,7 +71,8 @@ struct ResidentArgs {
     const int* seg_cell_start;    // per-cell segment lists (see SegGrid)
     const int* seg_cell_ids;
     const float4* par;      // [N] (radius, v_max, preferred speed, 0)
-    const float2* goal;     // [N]
+    float2* goal;           // [N] current goals (advanced in place with a goal queue)
+    GoalQueue goals;        // goal queue (q = 0: none)
     float4* state;          // [N] (px, py, vx, vy)
     const float2* robot_vel;  // [n_steps][robot_stride] or null (keep current)
     int robot_stride;       // entries per step in robot_vel (normally E)
@@ -127,7 +136,8 @@ struct TiledStepArgs {
     float4* state_out;        // [N] state after the step
     const float2* robot_vel;  // [E] commands of this step, or null (keep current)
     const float4* par;
-    const float2* goal;
+    float2* goal;             // [N] current goals (advanced in tiled_count with a goal queue)
+    GoalQueue goals;
     const float4* segs;
     const int* seg_cell_start;  // [cells + 1 per env] per-cell segment lists
     const int* seg_cell_ids;

@@ -264,7 +264,7 @@ extern "C" crowd_status crowd_step_noalloc(int32_t n_agents, const float* state_
     a.state_out = (float4*)state_out;
     a.robot_vel = nullptr;
     a.par = (const float4*)agent_params;
-    a.goal = (const float2*)goals;
+    a.goal = const_cast<float2*>((const float2*)goals);  // read only: no goal queue here (a.goals.q == 0)
     a.segs = (const float4*)segments;
     a.seg_cell_start = seg_start;
     a.seg_cell_ids = seg_ids;

@@ -402,6 +402,35 @@ def serving_stream(seed=0, rate=200.0, duration_s=10.0, n_lo=32, n_hi=2048, max_
     return reqs
 
 
+def goal_queue(scene: Scene, n_goals: int, seed: int = 0, hop: float | None = None) -> np.ndarray:
+    """Goal queues [N][n_goals][2] for crowd_set_goal_queue: goal 0 is the
+    scene's goal; each later goal is drawn uniformly in the environment's
+    box of starts and goals (or, with `hop`, within +-hop m of the previous
+    goal, clipped to that box), at least r + CLEARANCE from every segment."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    q = np.zeros((scene.n_agents, n_goals, 2), np.float32)
+    q[:, 0] = scene.goal
+    es, ss = scene.env_start, scene.seg_start
+    for e in range(scene.n_envs):
+        a, b = int(es[e]), int(es[e + 1])
+        if a == b:
+            continue
+        pts = np.concatenate([scene.pos[a:b], scene.goal[a:b]])
+        lo, hi = pts.min(0), pts.max(0)
+        segs = scene.segments[ss[e]:ss[e + 1]]
+        for i in range(a, b):
+            for k in range(1, n_goals):
+                for _ in range(1000):
+                    if hop is None:
+                        c = rng.uniform(lo, hi)
+                    else:
+                        c = np.clip(q[i, k - 1] + rng.uniform(-hop, hop, 2), lo, hi)
+                    if len(segs) == 0 or _seg_point_dist(c[0], c[1], segs).min() >= scene.radius[i] + CLEARANCE:
+                        break
+                q[i, k] = c
+    return q
+
+
 def make(name: str, seed: int = 0, **kw) -> Scene:
     return {"plain_square": plain_square, "urban_block": urban_block, "uneven_batch": uneven_batch,
             "dense_crowd": dense_crowd}[name](seed=seed, **kw)

@@ -89,5 +89,7 @@ def test_bad_arguments_rejected_on_host(lib, over, msg):
 def test_null_handle_calls_fail_cleanly(lib):
     assert lib.crowd_step(None, C.c_float(0.1), None, 0, 1) == cw.CROWD_EINVAL
     assert lib.crowd_read_state(None, None, 0) == cw.CROWD_EINVAL
+    assert lib.crowd_set_goal_queue(None, 2, None, 1, 0) == cw.CROWD_EINVAL
+    assert lib.crowd_read_goal_index(None, None) == cw.CROWD_EINVAL
     assert lib.crowd_destroy(None) == cw.CROWD_OK
     assert lib.crowd_num_agents(None) == 0

@@ -499,3 +499,91 @@ def test_agent_order_and_deferred_fallback_change_no_bit():
         if ref is None:
             ref = out
         assert np.array_equal(out, ref), (block, coop, order, split)
+
+
+# ----------------------------------------------------------------------------- goal queues
+
+def teacher_forced_goals(scene, queue, cyclic, steps, flags=0):
+    """Teacher forcing with goal queues: the host moves goals on with the
+    oracle's rule from the teacher state; the GPU does the same inside the
+    step.  Returns the worst velocity error, neighbour mismatches, goal-index
+    mismatches and the number of goal changes."""
+    from paper_2505_00690_gb300 import crowd as cw
+
+    cr = _crowd(scene, cw.CROWD_FLAG_EXPORT_NEIGHBORS | flags)
+    cr.set_goal_queue(queue, cyclic=cyclic)
+    o = oracle.OracleScene(scene)
+    robot_rows = np.zeros(scene.n_agents, bool)
+    for e in range(scene.n_envs):
+        if scene.robot_index[e] >= 0:
+            robot_rows[scene.env_start[e] + scene.robot_index[e]] = True
+    S = scene.state().astype(np.float32)
+    goal, idx = queue[:, 0].astype(np.float64), np.zeros(scene.n_agents, np.int64)
+    worst, mism, gmis = 0.0, 0, 0
+    for k in range(steps):
+        rv = scene.robot_vel_at(k).astype(np.float32)
+        goal, idx = oracle.advance_goals(S[:, :2], scene.radius, goal, idx, queue, cyclic, skip=robot_rows)
+        cr.set_state(S)
+        cr.step(rv[None], n_steps=1)
+        G = cr.state()
+        gmis += int((cr.goal_index() != idx).sum())
+        po, vo, nbO, st = o.step(S[:, :2], S[:, 2:], rv, goal=goal)
+        if scene.max_neighbors:
+            mism += int(np.any(cr.neighbors() != nbO, axis=1).sum())
+        worst = max(worst, float(np.abs(G[:, 2:].astype(np.float64) - vo).max()))
+        S = np.concatenate([po, vo], 1).astype(np.float32)
+    cr.close()
+    return worst, mism, gmis, int(idx.sum())
+
+
+def test_goal_queue_lone_agent_on_gpu():
+    """The hand-derived turns of the oracle pin: goal 1 from step 97, goal 2
+    from step 194, then the last goal kept."""
+    from paper_2505_00690_gb300 import crowd as cw
+
+    q = np.array([[(10.0, 0.0), (10.0, 10.0), (0.0, 10.0)]], np.float32)
+    sc = one_env([(0.0, 0.0)], [(0.0, 0.0)], q[:, 0], 0.35, 1.0)
+    cr = cw.Crowd(sc)
+    cr.set_goal_queue(q, cyclic=False)
+    seen = []
+    for _ in range(400):
+        cr.step(n_steps=1)
+        seen.append(int(cr.goal_index()[0]))
+    # the index read after step k was set at the start of step k
+    seen = np.array(seen)
+    assert np.nonzero(seen == 1)[0][0] == 97 and np.nonzero(seen == 2)[0][0] == 194 and seen.max() == 2
+    assert np.allclose(cr.state()[0, :2], [0.0, 10.0], atol=1e-5)
+    cr.close()
+
+
+@pytest.mark.parametrize("flags", [0, 8])
+def test_goal_queue_teacher_forced(flags):
+    """Urban blocks with 6-goal cyclic queues hopping <= 4 m: hundreds of goal
+    changes; identical goal counters, bit-exact neighbours, 1e-4 m/s."""
+    sc = scenes.urban_block(3, n_envs=4, steps=150)
+    q = scenes.goal_queue(sc, 6, seed=1, hop=4.0)
+    q[:, 0] = sc.pos + np.clip(q[:, 0] - sc.pos, -2.0, 2.0)  # first goals close by, too
+    worst, mism, gmis, changes = teacher_forced_goals(sc, q, True, 150, flags=flags)
+    assert changes > 200, changes
+    assert gmis == 0 and mism == 0
+    assert worst <= VEL_TOL, worst
+
+
+def test_goal_queue_multi_step_equals_single_steps():
+    from paper_2505_00690_gb300 import crowd as cw
+
+    sc = scenes.urban_block(4, n_envs=6, steps=120)
+    q = scenes.goal_queue(sc, 4, seed=2, hop=3.0)
+    outs = []
+    for chunks in ((120,), (1,) * 120, (50, 7, 63)):
+        cr = cw.Crowd(sc)
+        cr.set_goal_queue(q, cyclic=True)
+        k = 0
+        for n in chunks:
+            cr.step(sc.robot_vel[k:k + n], n_steps=n)
+            k += n
+        outs.append((cr.state(), cr.goal_index()))
+        cr.close()
+    for st, gi in outs[1:]:
+        assert np.array_equal(st, outs[0][0]) and np.array_equal(gi, outs[0][1])
+    assert outs[0][1].sum() > 50

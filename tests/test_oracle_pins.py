@@ -77,6 +77,60 @@ def test_lone_agent_closed_form():
     assert arrive == 80  # 10 m at 0.125 m per step: the 80th step starts exactly s*dt away and lands
 
 
+# ----------------------------------------------------------------------------- goal queues
+
+def _walk_queue(queue, cyclic, steps, r=0.35, s=1.0, dt=0.1):
+    """A lone agent from (0, 0) through a goal queue; returns the goal index at
+    the start of every step and the final position."""
+    q = np.asarray(queue, np.float32)[None]
+    sc = one_env([(0.0, 0.0)], [(0.0, 0.0)], [q[0, 0]], r, s, dt=dt)
+    o = oracle.OracleScene(sc)
+    pos, vel = np.zeros((1, 2)), np.zeros((1, 2))
+    goal, idx = q[:, 0].astype(np.float64), np.zeros(1, np.int64)
+    seen = []
+    for _ in range(steps):
+        goal, idx = oracle.advance_goals(pos, sc.radius, goal, idx, q, cyclic)
+        seen.append(int(idx[0]))
+        pos, vel, _, _ = o.step(pos, vel, goal=goal)
+    return np.array(seen), pos[0]
+
+
+def test_goal_queue_lone_agent_turns_within_reach():
+    """Speed 1 m/s, dt 0.1 s, r 0.35 m, goals (10, 0) -> (10, 10) -> (0, 10).
+    Hand-derived: the start of step k finds the agent 0.1 k m along the first
+    leg, so it is within 0.35 m of (10, 0) first at k = 97 (x = 9.7); the
+    second leg from (9.7, 0) is sqrt(0.3^2 + 10^2) = 10.0045 m long, so the
+    agent is within reach of (10, 10) after ceil((10.0045 - 0.35) / 0.1) = 97
+    more steps, at k = 194.  The queue is not cyclic: (0, 10) stays the goal,
+    the agent lands on it by the arrive rule and stops."""
+    seen, final = _walk_queue([(10.0, 0.0), (10.0, 10.0), (0.0, 10.0)], cyclic=False, steps=400)
+    assert np.nonzero(seen == 1)[0][0] == 97
+    assert np.nonzero(seen == 2)[0][0] == 194
+    assert seen[-1] == 2 and seen.max() == 2
+    assert np.allclose(final, [0.0, 10.0], atol=1e-12)
+
+
+def test_goal_queue_cyclic_shuttle():
+    """Goals (1, 0) and (0, 0), cyclic: out to x = 0.7 (within 0.35 of 1, step
+    7), back to x = 0.3 (step 11), out again to 0.7 (step 15): the index grows
+    every 4 steps after the first 7."""
+    seen, _ = _walk_queue([(1.0, 0.0), (0.0, 0.0)], cyclic=True, steps=40)
+    steps_at = [int(np.nonzero(seen == k)[0][0]) for k in range(1, 9)]
+    assert steps_at == [7, 11, 15, 19, 23, 27, 31, 35]
+
+
+def test_goal_queue_reach_boundary_and_robot():
+    """|g - p|^2 == r^2 exactly moves on (<=); one ulp beyond does not; the
+    robot row never moves on."""
+    q = np.array([[[0.375, 0.0], [5.0, 5.0]], [[np.nextafter(np.float32(0.375), np.float32(1)), 0.0], [5.0, 5.0]],
+                  [[0.0, 0.0], [5.0, 5.0]]], np.float32)
+    pos = np.zeros((3, 2))
+    g, k = oracle.advance_goals(pos, np.full(3, 0.375, np.float32), q[:, 0], np.zeros(3), q, cyclic=True,
+                                skip=[False, False, True])
+    assert list(k) == [1, 0, 0]
+    assert np.array_equal(g[0], [5.0, 5.0]) and np.array_equal(g[1], q[1, 0]) and np.array_equal(g[2], [0.0, 0.0])
+
+
 # ----------------------------------------------------------------------------- O3 closed form
 
 @pytest.mark.parametrize("half_gap,steps", [((4.0, 0.0), 400), ((0.0, -4.0), 400), ((3.0, 4.0), 20),
