@@ -337,6 +337,43 @@ crowd_status crowd_step_noalloc(int32_t n_agents, const float* state_in, float* 
                                 const float* goals, int32_t robot_index, int32_t n_segments, const float* segments,
                                 const float* box, const crowd_params* p, float dt, void* cuda_stream);
 
+/* ---- Occupancy-map front end (the step before the crowd step: the paper's
+ * crowds live on generated maps of traversable ground and static objects,
+ * with start and end points sampled on the traversable part, Sec. 3.1-3.2;
+ * the raster form of such a map and these calls are this library's).
+ *
+ * occ: DEVICE [H][W] bytes, nonzero = obstacle; cell (x, y) covers
+ * [x0 + x*cell, x0 + (x+1)*cell) x [y0 + y*cell, y0 + (y+1)*cell); W, H in
+ * [1, 32768]; closed != 0: everything outside the map is obstacle (walls
+ * round it), else free.  Coordinates are x0 + i*cell with the product and
+ * the sum rounded to FP32 separately.  Both calls run on `stream`, allocate
+ * and free temporary device memory, and wait for the stream before they
+ * return.
+ *
+ * crowd_map_segments: the boundary between free and obstacle cells as
+ * maximal axis-aligned segments [n][4] (ax, ay, bx, by) into DEVICE
+ * `segments`, each directed with the free side on its left: horizontal lines
+ * y = y0 + j*cell (j = 0..H) first, then vertical lines (i = 0..W), along each
+ * line in increasing coordinate.  *n_segments gets the count; if it exceeds
+ * max_segments nothing is written and CROWD_EINVAL is returned (call again
+ * with a larger buffer). */
+crowd_status crowd_map_segments(const uint8_t* occ, int32_t W, int32_t H, float cell, float x0, float y0,
+                                int32_t closed, int32_t max_segments, float* segments, int32_t* n_segments,
+                                void* stream);
+
+/* crowd_map_sample: n_points points [n][2] into DEVICE `points`, uniform over
+ * the cells that are free and have no obstacle (and, when closed, no outside)
+ * within `clearance` cells in x and y (0..CROWD_MAP_MAX_CLEARANCE).  Point k
+ * draws (u0, u1, u2, u3) = Philox4x32-10(counter (k, stream_id, 0, 0), key
+ * (seed low, seed high)); it lies in eligible cell floor(u0*M / 2^32) (M
+ * eligible cells in row-major order) at fractions (u1 >> 8)/2^24 and
+ * (u2 >> 8)/2^24 of the cell.  *n_eligible gets M; with n_points > 0 and
+ * M = 0 the call fails with CROWD_EINVAL. */
+#define CROWD_MAP_MAX_CLEARANCE 64
+crowd_status crowd_map_sample(const uint8_t* occ, int32_t W, int32_t H, float cell, float x0, float y0,
+                              int32_t closed, int32_t clearance, uint64_t seed, uint32_t stream_id, int32_t n_points,
+                              float* points, int32_t* n_eligible, void* stream);
+
 /* Message for the calling thread's last failed call ("" if none). */
 const char* crowd_last_error(void);
 
