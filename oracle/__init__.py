@@ -37,7 +37,8 @@ FALLBACK_STATUS = 1
 
 class Params(C.Structure):
     _fields_ = [("tau", C.c_double), ("tau_obst", C.c_double), ("neighbor_dist", C.c_double),
-                ("dt", C.c_double), ("robot_alpha", C.c_double), ("max_neighbors", C.c_int32)]
+                ("dt", C.c_double), ("robot_alpha", C.c_double), ("max_neighbors", C.c_int32),
+                ("seg_mode", C.c_int32)]
 
 
 class Line(C.Structure):
@@ -73,6 +74,7 @@ def lib():
             L.or_obstacles.restype = C.c_int
             L.or_agent_line.argtypes = [d] * 13 + [C.c_int, C.c_int, C.POINTER(Line)]
             L.or_obstacle_line.argtypes = [d] * 6 + [pd, d, d, C.POINTER(Line)]
+            L.or_obstacle_line_vd.argtypes = [d] * 6 + [pd, d, d, C.POINTER(Line)]
             L.or_lp2.argtypes = [C.POINTER(Line), C.c_int, d, d, d, pd, pd]
             L.or_lp2.restype = C.c_int
             L.or_fallback.argtypes = [C.POINTER(Line), C.c_int, C.c_int, d, d, d, pd, pd, pd]
@@ -172,6 +174,15 @@ def obstacle_line(p, v, r, vmax, seg, tau_o, dt):
     return np.array([ln.qx, ln.qy]), np.array([ln.nx, ln.ny])
 
 
+def obstacle_line_vd(p, v, r, vmax, seg, tau_o, dt):
+    """O4v (velocity-dependent segment half-plane): returns (q, n)."""
+    ln = Line()
+    s = _f64(seg).reshape(4)
+    lib().or_obstacle_line_vd(float(p[0]), float(p[1]), float(v[0]), float(v[1]), float(r), float(vmax),
+                              _p(s, C.c_double), float(tau_o), float(dt), C.byref(ln))
+    return np.array([ln.qx, ln.qy]), np.array([ln.nx, ln.ny])
+
+
 def _lines(lines):
     arr = (Line * max(len(lines), 1))()
     for k, (q, n) in enumerate(lines):
@@ -205,7 +216,7 @@ def _f32(x):
 def scene_params(scene):
     """Scene parameters as the FP32 values the crowd library receives, held in FP64."""
     return Params(_f32(scene.tau), _f32(scene.tau_obst), _f32(scene.neighbor_dist), _f32(scene.dt),
-                  _f32(scene.robot_responsibility), scene.max_neighbors)
+                  _f32(scene.robot_responsibility), scene.max_neighbors, int(getattr(scene, "segment_mode", 0)))
 
 
 class OracleScene:

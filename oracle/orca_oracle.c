@@ -52,6 +52,7 @@ typedef struct {
     double dt;
     double robot_alpha; /* share of responsibility an agent takes against the robot */
     int32_t max_neighbors; /* K */
+    int32_t seg_mode;   /* 0: O4 segment half-plane; 1: O4v velocity-dependent */
 } or_params;
 
 typedef struct {
@@ -266,6 +267,106 @@ void or_obstacle_line(double px, double py, double vx, double vy, double r, doub
     out->ny = -my;
 }
 
+/* ---------------------------------------------------------------- O4v --- */
+/* Velocity-dependent half-plane of agent p (radius r, velocity v) against
+ * segment s (the obstacle treatment of the method the paper cites, for one
+ * segment on its own).  When the agent is clear of the segment (d > r):
+ *   C = the capsule [a - p, b - p] + D(r); its truncated velocity obstacle
+ *   is the union of s*C for s >= 1/tau_o, bounded by the two legs (the rays
+ *   from 0 tangent to C, beyond the tangent points) and by the part of
+ *   C/tau_o that faces 0 (outward normal u with u.X < 0).  X = the point of
+ *   that boundary nearest v, n = the outward normal there; the agent takes
+ *   the whole responsibility: (v' - X).n >= 0.  Candidates, each the nearest
+ *   point of one piece: the flat side of C/tau_o towards 0 (when it faces
+ *   0), the two end-cap arcs that face 0 (the radial point, when it lies on
+ *   the arc; otherwise an end of the arc, which the flat side or a leg
+ *   covers), and the two leg rays; the first of equally near pieces wins
+ *   (flat, cap a, cap b, left, right).
+ * When it overlaps (d <= r): as O4. */
+static void or_leg(double X0, double X1, double r, int left, double* ux, double* uy, double* len)
+{
+    double d2 = X0 * X0 + X1 * X1;
+    double l = sqrt(d2 - r * r);
+    if (left) { *ux = (X0 * l - X1 * r) / d2; *uy = (X0 * r + X1 * l) / d2; }
+    else      { *ux = (X0 * l + X1 * r) / d2; *uy = (-X0 * r + X1 * l) / d2; }
+    *len = l;
+}
+
+void or_obstacle_line_vd(double px, double py, double vx, double vy, double r, double vmax,
+                         const double* s, double tau_o, double dt, or_line* out)
+{
+    double cx, cy;
+    or_closest_on_segment(px, py, s, &cx, &cy);
+    double dx = cx - px, dy = cy - py;
+    if (sqrt(dx * dx + dy * dy) <= r) {
+        or_obstacle_line(px, py, vx, vy, r, vmax, s, tau_o, dt, out);
+        return;
+    }
+    double A0 = s[0] - px, A1 = s[1] - py, B0 = s[2] - px, B1 = s[3] - py;
+    /* legs: of the two end disks' tangents, the outermost on each side */
+    double la0, la1, lal, lb0, lb1, lbl, ra0, ra1, ral, rb0, rb1, rbl;
+    or_leg(A0, A1, r, 1, &la0, &la1, &lal);
+    or_leg(B0, B1, r, 1, &lb0, &lb1, &lbl);
+    or_leg(A0, A1, r, 0, &ra0, &ra1, &ral);
+    or_leg(B0, B1, r, 0, &rb0, &rb1, &rbl);
+    double L0, L1, Ll, R0, R1, Rl;
+    if (la0 * lb1 - la1 * lb0 > 0.0) { L0 = lb0; L1 = lb1; Ll = lbl; } else { L0 = la0; L1 = la1; Ll = lal; }
+    if (ra0 * rb1 - ra1 * rb0 < 0.0) { R0 = rb0; R1 = rb1; Rl = rbl; } else { R0 = ra0; R1 = ra1; Rl = ral; }
+    double best = INFINITY, X0 = 0.0, X1 = 0.0, N0 = 0.0, N1 = 0.0;
+    /* the part of C / tau_o that faces 0: the flat side towards 0 (if it
+     * faces 0) and the arcs of the two end caps that face 0 */
+    {
+        double rt = r / tau_o;
+        double a0 = A0 / tau_o, a1 = A1 / tau_o, b0 = B0 / tau_o, b1 = B1 / tau_o;
+        double e0 = B0 - A0, e1 = B1 - A1, el = sqrt(e0 * e0 + e1 * e1);
+        if (el > 0.0) {
+            double m0 = -e1 / el, m1 = e0 / el;       /* unit normal of the segment, towards 0 */
+            if (m0 * A0 + m1 * A1 > 0.0) { m0 = -m0; m1 = -m1; }
+            if (m0 * A0 + m1 * A1 < -r) {            /* the flat side faces 0 */
+                double f0 = a0 + rt * m0, f1 = a1 + rt * m1, g0 = b0 - a0, g1 = b1 - a1;
+                double t = ((vx - f0) * g0 + (vy - f1) * g1) / (g0 * g0 + g1 * g1);
+                if (t < 0.0) t = 0.0;
+                if (t > 1.0) t = 1.0;
+                double x0 = f0 + t * g0, x1 = f1 + t * g1;
+                double dd = sqrt((vx - x0) * (vx - x0) + (vy - x1) * (vy - x1));
+                if (dd < best) { best = dd; X0 = x0; X1 = x1; N0 = m0; N1 = m1; }
+            }
+        }
+        for (int cap = 0; cap < 2; ++cap) {
+            double c0 = cap ? b0 : a0, c1 = cap ? b1 : a1;        /* cap centre (scaled) */
+            double o0 = cap ? A0 - B0 : B0 - A0, o1 = cap ? A1 - B1 : B1 - A1; /* towards the other end */
+            double w0 = vx - c0, w1 = vy - c1, wl = sqrt(w0 * w0 + w1 * w1);
+            if (!(wl > 0.0)) continue;
+            double u0 = w0 / wl, u1 = w1 / wl;
+            /* on this cap's half circle, and facing 0: u.(centre) < -r/tau_o */
+            if (u0 * o0 + u1 * o1 > 0.0) continue;
+            if (!(u0 * c0 + u1 * c1 < -rt)) continue;
+            double dd = fabs(wl - rt);
+            if (dd < best) { best = dd; X0 = c0 + rt * u0; X1 = c1 + rt * u1; N0 = u0; N1 = u1; }
+        }
+    }
+    /* left leg: outward normal to its left */
+    {
+        double t = vx * L0 + vy * L1, tmin = Ll / tau_o;
+        if (t < tmin) t = tmin;
+        double x0 = t * L0, x1 = t * L1;
+        double dd = sqrt((vx - x0) * (vx - x0) + (vy - x1) * (vy - x1));
+        if (dd < best) { best = dd; X0 = x0; X1 = x1; N0 = -L1; N1 = L0; }
+    }
+    /* right leg: outward normal to its right */
+    {
+        double t = vx * R0 + vy * R1, tmin = Rl / tau_o;
+        if (t < tmin) t = tmin;
+        double x0 = t * R0, x1 = t * R1;
+        double dd = sqrt((vx - x0) * (vx - x0) + (vy - x1) * (vy - x1));
+        if (dd < best) { best = dd; X0 = x0; X1 = x1; N0 = R1; N1 = -R0; }
+    }
+    out->qx = X0;
+    out->qy = X1;
+    out->nx = N0;
+    out->ny = N1;
+}
+
 /* ---------------------------------------------------------------- O5 ---- */
 /* Minimise |v' - pref| on line k, inside the disk of radius vmax and the
  * previous lines 0..k-1.  Returns 0 if that set is empty. */
@@ -441,9 +542,14 @@ int or_step(int32_t n_envs, const int64_t* env_start, const double* radius, cons
             int32_t* oids = (int32_t*)malloc(sizeof(int32_t) * (size_t)(ns > 0 ? ns : 1));
             int no = or_obstacles(ns, S, P[2 * i], P[2 * i + 1], radius[g] + tau_o * vmax[g], oids);
             or_line* L = (or_line*)malloc(sizeof(or_line) * (size_t)(no + nn + 1));
-            for (int k = 0; k < no; ++k)
-                or_obstacle_line(P[2 * i], P[2 * i + 1], OR_VEL(i, 0), OR_VEL(i, 1), radius[g], vmax[g],
-                                 S + 4 * oids[k], tau_o, prm->dt, &L[k]);
+            for (int k = 0; k < no; ++k) {
+                if (prm->seg_mode == 1)
+                    or_obstacle_line_vd(P[2 * i], P[2 * i + 1], OR_VEL(i, 0), OR_VEL(i, 1), radius[g], vmax[g],
+                                        S + 4 * oids[k], tau_o, prm->dt, &L[k]);
+                else
+                    or_obstacle_line(P[2 * i], P[2 * i + 1], OR_VEL(i, 0), OR_VEL(i, 1), radius[g], vmax[g],
+                                     S + 4 * oids[k], tau_o, prm->dt, &L[k]);
+            }
             for (int k = 0; k < nn; ++k) {
                 int j = ids[k];
                 double alpha = (j == robot) ? prm->robot_alpha : 0.5;

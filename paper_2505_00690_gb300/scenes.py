@@ -50,6 +50,7 @@ class Scene:
     max_neighbors: int = MAX_NEIGHBORS
     dt: float = DT
     robot_responsibility: float = 0.5
+    segment_mode: int = 0  # 0: segment half-plane tangent at the VO point nearest 0; 1: velocity-dependent
     steps: int = 1
     robot_vel: np.ndarray | None = None  # float32 [steps, E, 2] m/s (commanded)
     meta: dict = field(default_factory=dict)
@@ -95,7 +96,7 @@ class Scene:
             segments=self.segments[si].copy() if len(si) else np.zeros((0, 4), np.float32),
             tau=self.tau, tau_obst=self.tau_obst, neighbor_dist=self.neighbor_dist,
             max_neighbors=self.max_neighbors, dt=self.dt,
-            robot_responsibility=self.robot_responsibility, steps=self.steps,
+            robot_responsibility=self.robot_responsibility, segment_mode=self.segment_mode, steps=self.steps,
             robot_vel=None if self.robot_vel is None else self.robot_vel[:, envs].copy(),
             meta=dict(self.meta),
         )

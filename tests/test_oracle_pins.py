@@ -7,6 +7,7 @@ t*v lands in D(p, r) for some t in [0, tau]), brute-force vertex enumeration
 of the LP, and invariants ORCA guarantees (Sec. 3.2 of the paper with the
 method it cites for the collision-avoidance rule).
 """
+import dataclasses
 import math
 
 import numpy as np
@@ -261,6 +262,129 @@ def test_agent_line_matches_vo_geometry(seed):
     n_bf = u_bf / np.linalg.norm(u_bf) * (1.0 if inside else -1.0)
     assert np.allclose(n, n_bf, atol=1e-4)
     assert abs(np.linalg.norm(n) - 1.0) < 1e-12
+
+
+def _seg_dist_many(X, A, B):
+    """Distance from points X [..., 2] to segment [A, B]."""
+    e = B - A
+    t = np.clip(((X - A) @ e) / (e @ e), 0.0, 1.0)
+    return np.linalg.norm(X - (A + t[..., None] * e), axis=-1)
+
+
+def _in_cvo_many(P, A, B, r, tau):
+    """Definition for a segment: v is in the truncated VO of the capsule
+    [A, B] + D(r) iff t*v comes within r of [A, B] for some t in [0, tau],
+    i.e. iff the segments [0, tau v] and [A, B] are closer than r."""
+    T = tau * P
+    d = np.minimum(_seg_dist_many(T, A, B), _seg_dist_many(np.zeros_like(T), A, B))
+    zero = np.zeros(2)
+    for X in (A, B):
+        e = T
+        ee = np.where((e * e).sum(-1) > 0, (e * e).sum(-1), 1.0)
+        t = np.clip((e @ X) / ee, 0.0, 1.0)
+        d = np.minimum(d, np.linalg.norm(X - t[..., None] * e, axis=-1))
+    # proper crossing of the two segments: distance 0
+    cr = lambda o, a, b: (a[..., 0] - o[..., 0]) * (b[..., 1] - o[..., 1]) - (a[..., 1] - o[..., 1]) * (b[..., 0] - o[..., 0])
+    Z = np.broadcast_to(zero, T.shape)
+    Ab, Bb = np.broadcast_to(A, T.shape), np.broadcast_to(B, T.shape)
+    crossing = (np.sign(cr(Z, T, Ab)) * np.sign(cr(Z, T, Bb)) < 0) & (np.sign(cr(Ab, Bb, Z)) * np.sign(cr(Ab, Bb, T)) < 0)
+    return (d < r) | crossing
+
+
+def _nearest_cvo_boundary(v, A, B, r, tau, ndir=512, reach=12.0, step=2e-3):
+    """_nearest_boundary for the segment's VO (same search)."""
+    inside = bool(_in_cvo_many(v[None], A, B, r, tau)[0])
+    s = np.arange(step, reach, step)
+
+    def cross(thetas):
+        d = np.stack([np.cos(thetas), np.sin(thetas)], -1)
+        P = v[None, None, :] + s[None, :, None] * d[:, None, :]
+        change = _in_cvo_many(P, A, B, r, tau) != inside
+        first = np.where(change.any(1), change.argmax(1), -1)
+        out = np.full(len(thetas), np.inf)
+        for k in np.nonzero(first >= 0)[0]:
+            lo = 0.0 if first[k] == 0 else s[first[k] - 1]
+            hi = s[first[k]]
+            for _ in range(60):
+                mid = 0.5 * (lo + hi)
+                if bool(_in_cvo_many((v + mid * d[k])[None], A, B, r, tau)[0]) == inside:
+                    lo = mid
+                else:
+                    hi = mid
+            out[k] = hi
+        return out
+
+    thetas = np.linspace(0, 2 * math.pi, ndir, endpoint=False)
+    dists = cross(thetas)
+    k = int(np.argmin(dists))
+    a, b = thetas[k] - 2 * math.pi / ndir, thetas[k] + 2 * math.pi / ndir
+    g = (math.sqrt(5) - 1) / 2
+    c, d = b - g * (b - a), a + g * (b - a)
+    fc, fd = cross(np.array([c]))[0], cross(np.array([d]))[0]
+    for _ in range(50):
+        if fc < fd:
+            b, d, fd = d, c, fc
+            c = b - g * (b - a)
+            fc = cross(np.array([c]))[0]
+        else:
+            a, c, fc = c, d, fd
+            d = a + g * (b - a)
+            fd = cross(np.array([d]))[0]
+    th = 0.5 * (a + b)
+    dist = cross(np.array([th]))[0]
+    return dist * np.array([math.cos(th), math.sin(th)]), inside
+
+
+def test_velocity_segment_line_long_wall_closed_form():
+    """O4v against a long wall 5 m ahead (r 0.3, tau_o 2): the face of the VO
+    is the line v_y = (5 - 0.3) / 2 = 2.35, so walking at it or along it the
+    nearest boundary point is v's projection on that line and the normal -y
+    (the velocity-independent O4 line is the same there)."""
+    for v in ((0.0, 1.2), (1.2, 0.0), (-0.7, 0.4)):
+        q, n = oracle.obstacle_line_vd((0.0, 0.0), v, 0.3, 1.4, (-50.0, 5.0, 50.0, 5.0), 2.0, 0.1)
+        assert np.allclose(q, [v[0], 2.35], atol=1e-12) and np.allclose(n, [0.0, -1.0], atol=1e-12)
+
+
+def test_velocity_segment_line_leg_hand_case():
+    """Segment (-0.5, 3)-(0.5, 3), r 0.3, tau_o 2, v = (0.2, 2.0), inside the
+    VO: by hand, the right leg (tangent to the disk at (0.5, 3): direction
+    angle atan2(3, 0.5) - asin(0.3 / |(0.5, 3)|) = 1.3070 rad) is 0.328 m/s
+    away, the left one 0.714 and the face behind v does not face 0, so X is
+    v's projection on the right leg, (0.517, 1.914), with normal
+    (0.9654, -0.2607)."""
+    q, n = oracle.obstacle_line_vd((0.0, 0.0), (0.2, 2.0), 0.3, 1.4, (-0.5, 3.0, 0.5, 3.0), 2.0, 0.1)
+    assert np.allclose(q, [0.517, 1.914], atol=2e-3) and np.allclose(n, [0.9654, -0.2607], atol=2e-4)
+
+
+@pytest.mark.parametrize("seed", range(16))
+def test_velocity_segment_line_matches_vo_geometry(seed):
+    """X and n of O4v equal the nearest point of the segment VO's boundary
+    (brute force from the definition) and the outward normal there."""
+    rng = np.random.default_rng(500 + seed)
+    while True:
+        p = rng.uniform(-2, 2, 2)
+        a = p + rng.uniform(-4, 4, 2)
+        b = a + rng.uniform(-3, 3, 2)
+        r = rng.uniform(0.2, 0.45)
+        seg = np.concatenate([a, b])
+        e = b - a
+        t = np.clip(((p - a) @ e) / (e @ e), 0, 1)
+        if np.linalg.norm(a + t * e - p) > r + 0.1:
+            break
+    v = rng.uniform(-1.5, 1.5, 2)
+    tau = 2.0
+    q, n = oracle.obstacle_line_vd(p, v, r, 1.6, seg, tau, 0.1)
+    u_bf, inside = _nearest_cvo_boundary(v, a - p, b - p, r, tau)
+    assert np.linalg.norm(q - (v + u_bf)) < 1e-5, (q, v + u_bf)
+    n_bf = u_bf / np.linalg.norm(u_bf) * (1.0 if inside else -1.0)
+    assert np.allclose(n, n_bf, atol=1e-3), (n, n_bf)
+
+
+def test_velocity_segment_line_overlap_is_o4():
+    for v in ((0.3, -0.2), (0.0, 0.0)):
+        q1, n1 = oracle.obstacle_line_vd((0.0, 0.1), v, 0.3, 1.4, (-1.0, 0.0, 1.0, 0.0), 2.0, 0.1)
+        q0, n0 = oracle.obstacle_line((0.0, 0.1), v, 0.3, 1.4, (-1.0, 0.0, 1.0, 0.0), 2.0, 0.1)
+        assert np.array_equal(q1, q0) and np.array_equal(n1, n0)
 
 
 @pytest.mark.parametrize("seed", range(20))
@@ -592,7 +716,8 @@ def _check_step_invariants(o, sc, pos, vel, robot_vel, nv, st):
             assert np.linalg.norm(nv[g]) <= vmax * (1 + 1e-12) + 1e-15
             ids, _ = oracle.neighbors(pos[base:base + n], i, R, K)
             oids = oracle.obstacles(segs, pos[g], float(sc.radius[g]) + tau_o * vmax) if len(segs) else []
-            lines = [oracle.obstacle_line(pos[g], V[i], sc.radius[g], vmax, segs[s], tau_o, dt) for s in oids]
+            seg_line = oracle.obstacle_line_vd if prm.seg_mode == 1 else oracle.obstacle_line
+            lines = [seg_line(pos[g], V[i], sc.radius[g], vmax, segs[s], tau_o, dt) for s in oids]
             for j in ids:
                 alpha = ra if j == robot else 0.5
                 lines.append(oracle.agent_line(pos[g], V[i], sc.radius[g], pos[base + j], V[j],
@@ -608,9 +733,11 @@ def _check_step_invariants(o, sc, pos, vel, robot_vel, nv, st):
                         assert (nv[g] - q) @ nrm >= -1e-9
 
 
-@pytest.mark.parametrize("maker", ["plain", "urban"])
+@pytest.mark.parametrize("maker", ["plain", "urban", "urban_velocity_segments"])
 def test_rollout_invariants(maker):
     sc = plain_square(1, n=32) if maker == "plain" else urban_block(1, n_envs=2, n_peds=48, steps=40)
+    if maker == "urban_velocity_segments":
+        sc = dataclasses.replace(sc, segment_mode=1)
     o = oracle.OracleScene(sc)
     pos, vel = sc.pos.astype(np.float64), sc.vel.astype(np.float64)
     for k in range(40):
