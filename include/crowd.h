@@ -72,8 +72,13 @@ enum {
     CROWD_FLAG_EXPORT_NEIGHBORS = 1, /* keep the neighbour lists of the last step (crowd_read_neighbors) */
     CROWD_FLAG_STATS = 2,            /* accumulate rollout statistics (crowd_read_stats) */
     CROWD_FLAG_COUNT_WORK = 4,       /* count the algorithm's work items (crowd_read_work) */
-    CROWD_FLAG_FORCE_TILED = 8       /* run every environment on the tiled (global-memory) path; by
+    CROWD_FLAG_FORCE_TILED = 8,      /* run every environment on the tiled (global-memory) path; by
                                         default only environments of more than 2048 agents do */
+    CROWD_FLAG_VELOCITY_SEGMENTS = 16 /* segment half-planes tangent to the segment's truncated velocity
+                                         obstacle at its boundary point nearest the agent's current
+                                         velocity (full responsibility; the obstacle treatment of the
+                                         method the paper cites, each segment on its own) instead of at
+                                         its point nearest 0 */
 };
 
 /* Work counters (CROWD_FLAG_COUNT_WORK), summed over all agents and steps

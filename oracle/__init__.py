@@ -75,6 +75,8 @@ def lib():
             L.or_agent_line.argtypes = [d] * 13 + [C.c_int, C.c_int, C.POINTER(Line)]
             L.or_obstacle_line.argtypes = [d] * 6 + [pd, d, d, C.POINTER(Line)]
             L.or_obstacle_line_vd.argtypes = [d] * 6 + [pd, d, d, C.POINTER(Line)]
+            L.or_segment_covered.argtypes = [d, d, d, pd, d, C.POINTER(Line), C.c_int]
+            L.or_segment_covered.restype = C.c_int
             L.or_lp2.argtypes = [C.POINTER(Line), C.c_int, d, d, d, pd, pd]
             L.or_lp2.restype = C.c_int
             L.or_fallback.argtypes = [C.POINTER(Line), C.c_int, C.c_int, d, d, d, pd, pd, pd]
@@ -181,6 +183,17 @@ def obstacle_line_vd(p, v, r, vmax, seg, tau_o, dt):
     lib().or_obstacle_line_vd(float(p[0]), float(p[1]), float(v[0]), float(v[1]), float(r), float(vmax),
                               _p(s, C.c_double), float(tau_o), float(dt), C.byref(ln))
     return np.array([ln.qx, ln.qy]), np.array([ln.nx, ln.ny])
+
+
+def segment_covered(p, r, seg, tau_o, lines):
+    """O4v: whether an earlier segment line (q, n) already forbids the whole
+    velocity obstacle of `seg` (then the segment gets no line)."""
+    arr = (Line * max(1, len(lines)))()
+    for k, (q, n) in enumerate(lines):
+        arr[k] = Line(float(q[0]), float(q[1]), float(n[0]), float(n[1]))
+    s = _f64(seg).reshape(4)
+    return bool(lib().or_segment_covered(float(p[0]), float(p[1]), float(r), _p(s, C.c_double), float(tau_o), arr,
+                                         len(lines)))
 
 
 def _lines(lines):

@@ -367,6 +367,30 @@ void or_obstacle_line_vd(double px, double py, double vx, double vy, double r, d
     out->ny = N1;
 }
 
+/* O4v, segments already taken care of: segment s is given no line when an
+ * earlier segment line of the agent (one that leaves 0 allowed) forbids both
+ * end disks of s's cutoff capsule, (X - q).n + r/tau_o <= OR_EPS_COVERED for
+ * X = (a - p)/tau_o and (b - p)/tau_o: the whole velocity obstacle of s then
+ * lies in that line's forbidden half-plane (it is the union of the cutoff
+ * capsule scaled away from 0).  The agent must be clear of s. */
+#define OR_EPS_COVERED 1e-5
+int or_segment_covered(double px, double py, double r, const double* s, double tau_o, const or_line* L,
+                              int m)
+{
+    double cx, cy;
+    or_closest_on_segment(px, py, s, &cx, &cy);
+    if (sqrt((cx - px) * (cx - px) + (cy - py) * (cy - py)) <= r) return 0;
+    double a0 = (s[0] - px) / tau_o, a1 = (s[1] - py) / tau_o, b0 = (s[2] - px) / tau_o, b1 = (s[3] - py) / tau_o;
+    double rt = r / tau_o;
+    for (int l = 0; l < m; ++l) {
+        if (-(L[l].qx * L[l].nx + L[l].qy * L[l].ny) < -OR_EPS_COVERED) continue;  /* 0 not allowed */
+        double va = (a0 - L[l].qx) * L[l].nx + (a1 - L[l].qy) * L[l].ny + rt;
+        double vb = (b0 - L[l].qx) * L[l].nx + (b1 - L[l].qy) * L[l].ny + rt;
+        if (va <= OR_EPS_COVERED && vb <= OR_EPS_COVERED) return 1;
+    }
+    return 0;
+}
+
 /* ---------------------------------------------------------------- O5 ---- */
 /* Minimise |v' - pref| on line k, inside the disk of radius vmax and the
  * previous lines 0..k-1.  Returns 0 if that set is empty. */
@@ -542,14 +566,20 @@ int or_step(int32_t n_envs, const int64_t* env_start, const double* radius, cons
             int32_t* oids = (int32_t*)malloc(sizeof(int32_t) * (size_t)(ns > 0 ? ns : 1));
             int no = or_obstacles(ns, S, P[2 * i], P[2 * i + 1], radius[g] + tau_o * vmax[g], oids);
             or_line* L = (or_line*)malloc(sizeof(or_line) * (size_t)(no + nn + 1));
+            int kept = 0;
             for (int k = 0; k < no; ++k) {
-                if (prm->seg_mode == 1)
-                    or_obstacle_line_vd(P[2 * i], P[2 * i + 1], OR_VEL(i, 0), OR_VEL(i, 1), radius[g], vmax[g],
-                                        S + 4 * oids[k], tau_o, prm->dt, &L[k]);
-                else
-                    or_obstacle_line(P[2 * i], P[2 * i + 1], OR_VEL(i, 0), OR_VEL(i, 1), radius[g], vmax[g],
-                                     S + 4 * oids[k], tau_o, prm->dt, &L[k]);
+                const double* sg = S + 4 * oids[k];
+                if (prm->seg_mode == 1) {
+                    if (or_segment_covered(P[2 * i], P[2 * i + 1], radius[g], sg, tau_o, L, kept)) continue;
+                    or_obstacle_line_vd(P[2 * i], P[2 * i + 1], OR_VEL(i, 0), OR_VEL(i, 1), radius[g], vmax[g], sg,
+                                        tau_o, prm->dt, &L[kept]);
+                } else {
+                    or_obstacle_line(P[2 * i], P[2 * i + 1], OR_VEL(i, 0), OR_VEL(i, 1), radius[g], vmax[g], sg,
+                                     tau_o, prm->dt, &L[kept]);
+                }
+                ++kept;
             }
+            no = kept;
             for (int k = 0; k < nn; ++k) {
                 int j = ids[k];
                 double alpha = (j == robot) ? prm->robot_alpha : 0.5;

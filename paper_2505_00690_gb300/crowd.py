@@ -22,6 +22,7 @@ CROWD_FLAG_EXPORT_NEIGHBORS = 1
 CROWD_FLAG_STATS = 2
 CROWD_FLAG_COUNT_WORK = 4
 CROWD_FLAG_FORCE_TILED = 8
+CROWD_FLAG_VELOCITY_SEGMENTS = 16
 STATUS_NAMES = {0: "CROWD_OK", 1: "CROWD_EINVAL", 2: "CROWD_ENOMEM", 3: "CROWD_ECUDA", 4: "CROWD_EDEVICE",
                 5: "CROWD_ESTATE"}
 
@@ -237,6 +238,8 @@ def crowd_last_error():
 
 def params_for(scene, flags=0):
     f = lambda x: float(np.float32(x))
+    if getattr(scene, "segment_mode", 0) == 1:
+        flags |= CROWD_FLAG_VELOCITY_SEGMENTS
     return crowd_params(f(scene.tau), f(scene.tau_obst), f(scene.neighbor_dist), int(scene.max_neighbors),
                         f(scene.robot_responsibility), int(flags))
 

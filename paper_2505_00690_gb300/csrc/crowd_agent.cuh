@@ -87,7 +87,75 @@ struct AgentParams {
     int K;
     const float4* segs;  // segments of all environments
     int* err;            // device error word
+    int seg_vd;          // 1: velocity-dependent segment half-planes (obstacle_line_vd)
 };
+
+// Velocity-dependent mode: segment s gets no line when an earlier segment
+// line (one that leaves 0 allowed) forbids both end disks of its cutoff
+// capsule, (X - q).n + r/tau_o <= 1e-5 for X = (a - p)/tau_o, (b - p)/tau_o:
+// its whole velocity obstacle already lies in that line's forbidden
+// half-plane.  At a convex corner this drops the second edge, whose line
+// would nearly coincide with the first one's.  The agent must be clear of s.
+__device__ __forceinline__ bool segment_covered(float px, float py, float r, float4 s, float tau_o, const Line* L,
+                                                int m) {
+    float cx, cy;
+    if (!(seg_dist2(px, py, s, cx, cy) > r * r)) return false;
+    const float a0 = (s.x - px) / tau_o, a1 = (s.y - py) / tau_o, b0 = (s.z - px) / tau_o, b1 = (s.w - py) / tau_o;
+    const float rt = r / tau_o;
+    for (int l = 0; l < m; ++l) {
+        const Line ll = L[l];
+        if (-(ll.qx * ll.nx + ll.qy * ll.ny) < -1e-5f) continue;  // 0 not allowed
+        const float va = (a0 - ll.qx) * ll.nx + (a1 - ll.qy) * ll.ny + rt;
+        const float vb = (b0 - ll.qx) * ll.nx + (b1 - ll.qy) * ll.ny + rt;
+        if (va <= 1e-5f && vb <= 1e-5f) return true;
+    }
+    return false;
+}
+
+// Squared distance from p to segment s as the definition evaluates it in
+// FP64 (projection parameter clamped to [0, 1], closest point, squared
+// distance; every operation rounded separately).
+__device__ __forceinline__ double seg_dist2_fp64(float px, float py, float4 s) {
+    const double ex = __dsub_rn((double)s.z, (double)s.x), ey = __dsub_rn((double)s.w, (double)s.y);
+    const double dx = __dsub_rn((double)px, (double)s.x), dy = __dsub_rn((double)py, (double)s.y);
+    double t = __ddiv_rn(__dadd_rn(__dmul_rn(dx, ex), __dmul_rn(dy, ey)), __dadd_rn(__dmul_rn(ex, ex), __dmul_rn(ey, ey)));
+    t = t < 0.0 ? 0.0 : (t > 1.0 ? 1.0 : t);
+    const double cx = __dadd_rn((double)s.x, __dmul_rn(t, ex)), cy = __dadd_rn((double)s.y, __dmul_rn(t, ey));
+    const double qx = __dsub_rn((double)px, cx), qy = __dsub_rn((double)py, cy);
+    return __dadd_rn(__dmul_rn(qx, qx), __dmul_rn(qy, qy));
+}
+
+// With the covered rule the order of the segment lines matters, so runs of
+// FP32 keys within 1e-5 relative of their neighbour are ranked again by
+// (FP64 squared distance, id), the definition's order.
+static __device__ __noinline__ void repair_segment_order(float px, float py, const float4* segs, const float* okey,
+                                                         int* oid, int n) {
+    int s = 0;
+    while (s < n) {
+        int e = s;
+        while (e + 1 < n && okey[e + 1] - okey[e] <= 1e-5f * okey[e + 1]) ++e;
+        if (e > s) {
+            double kk[kMaxObstacleLines];
+            for (int q = s; q <= e; ++q) kk[q] = seg_dist2_fp64(px, py, __ldg(&segs[oid[q]]));
+            for (int q = s + 1; q <= e; ++q)
+                for (int z = q; z > s && (kk[z] < kk[z - 1] || (kk[z] == kk[z - 1] && oid[z] < oid[z - 1])); --z) {
+                    const double tk = kk[z];
+                    kk[z] = kk[z - 1];
+                    kk[z - 1] = tk;
+                    const int ti = oid[z];
+                    oid[z] = oid[z - 1];
+                    oid[z - 1] = ti;
+                }
+        }
+        s = e + 1;
+    }
+}
+
+// A4 line of one segment, in the mode of the step.
+__device__ __forceinline__ Line segment_line(const AgentParams& a, float4 me, float4 pr, float4 sg) {
+    return a.seg_vd ? obstacle_line_vd(me.x, me.y, me.z, me.w, pr.x, pr.y, sg, a.tau_o, a.dt)
+                    : obstacle_line(me.x, me.y, me.z, me.w, pr.x, pr.y, sg, a.tau_o, a.dt);
+}
 
 // Distance from p to the bounding box of a segment, squared (a cheap lower
 // bound of the segment distance used to skip far segments).
@@ -312,8 +380,17 @@ __device__ __forceinline__ float2 solve_velocity(const AgentParams& a, const Age
         oid[p] = s;
         ++no;
     }
-    for (int k = 0; k < no; ++k)
-        L[k] = obstacle_line(me.x, me.y, me.z, me.w, pr.x, pr.y, __ldg(&a.segs[seg0 + oid[k]]), a.tau_o, a.dt);
+    if (a.seg_vd) {
+        repair_segment_order(me.x, me.y, a.segs + seg0, okey, oid, no);
+        int kept = 0;
+        for (int k = 0; k < no; ++k) {
+            const float4 sg = __ldg(&a.segs[seg0 + oid[k]]);
+            if (!segment_covered(me.x, me.y, pr.x, sg, a.tau_o, L, kept)) L[kept++] = segment_line(a, me, pr, sg);
+        }
+        no = kept;
+    } else {
+        for (int k = 0; k < no; ++k) L[k] = segment_line(a, me, pr, __ldg(&a.segs[seg0 + oid[k]]));
+    }
 
     // A3: one reciprocal half-plane per neighbour, in list order (a rolled
     // loop: one copy of agent_line keeps the kernel's code small)

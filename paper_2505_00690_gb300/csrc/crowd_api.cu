@@ -357,6 +357,7 @@ crowd_status resident_steps(crowd_t h, float dt, const float2* rv, int n_steps, 
     a.par = h->par;
     a.goal = h->goal;
     a.goals = GoalQueue{h->goal_queue, h->goal_idx, h->goal_q, h->goal_cyclic};
+    a.seg_vd = (h->p.flags & CROWD_FLAG_VELOCITY_SEGMENTS) ? 1 : 0;
     a.state = h->state;
     a.robot_vel = rv;
     a.robot_stride = h->E;
@@ -399,6 +400,7 @@ TiledStepArgs tiled_args(crowd_t h, float dt, const float2* rv, int s, int n_ste
     a.par = h->par;
     a.goal = h->goal;
     a.goals = GoalQueue{h->goal_queue, h->goal_idx, h->goal_q, h->goal_cyclic};
+    a.seg_vd = (h->p.flags & CROWD_FLAG_VELOCITY_SEGMENTS) ? 1 : 0;
     a.segs = h->segs;
     a.seg_cell_start = h->seg_cell_start;
     a.seg_cell_ids = h->seg_cell_ids;

@@ -317,8 +317,22 @@ __device__ __forceinline__ float2 group_solve(const Grp<G>& g, const AgentParams
         oid[p] = s;
         ++no;
     }
-    for (int k = g.lane; k < no; k += G)
-        mine[k / G] = obstacle_line(me.x, me.y, me.z, me.w, pr.x, pr.y, __ldg(&a.segs[seg0 + oid[k]]), a.tau_o, a.dt);
+    if (a.seg_vd) {
+        // the kept set depends on the lines before it: every lane builds all
+        // of them, then keeps its share
+        repair_segment_order(me.x, me.y, a.segs + seg0, okey, oid, no);
+        Line all[kMaxObstacleLines];
+        int kept = 0;
+        for (int k = 0; k < no; ++k) {
+            const float4 sg = __ldg(&a.segs[seg0 + oid[k]]);
+            if (!segment_covered(me.x, me.y, pr.x, sg, a.tau_o, all, kept)) all[kept++] = segment_line(a, me, pr, sg);
+        }
+        no = kept;
+        for (int k = g.lane; k < no; k += G) mine[k / G] = all[k];
+    } else {
+        for (int k = g.lane; k < no; k += G)
+            mine[k / G] = segment_line(a, me, pr, __ldg(&a.segs[seg0 + oid[k]]));
+    }
 
     // A3: agent line s is global line no + s
 #pragma unroll

@@ -79,6 +79,7 @@ struct ResidentArgs {
     int n_steps;
     float dt, tau, tau_o, R, robot_alpha;
     int K;
+    int seg_vd;             // 1: velocity-dependent segment half-planes
     int* nbr_out;           // [N][K] or null: neighbour lists of the last step
     EnvStats* stats;        // [E] or null: accumulate statistics
     int* reach;             // [N] or null: 1-based step of first goal reach
@@ -150,6 +151,7 @@ struct TiledStepArgs {
     int halo_cap;             // agents the update kernel stages in shared memory
     float R, dt, tau, tau_o, robot_alpha;
     int K;
+    int seg_vd;               // 1: velocity-dependent segment half-planes
     int mode;                 // kTiledStep / kTiledStepCount / kTiledStatsOnly
     int* nbr_out;             // [N][K] or null
     EnvStats* stats;          // [E] or null

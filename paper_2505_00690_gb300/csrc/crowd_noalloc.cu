@@ -280,6 +280,7 @@ extern "C" crowd_status crowd_step_noalloc(int32_t n_agents, const float* state_
     a.tau = p->time_horizon;
     a.tau_o = tau_o;
     a.robot_alpha = p->robot_responsibility;
+    a.seg_vd = (p->flags & CROWD_FLAG_VELOCITY_SEGMENTS) ? 1 : 0;
     a.K = p->max_neighbors;
     a.mode = kTiledStep;
     a.step_index = &misc->step;

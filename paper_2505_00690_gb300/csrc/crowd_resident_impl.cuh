@@ -403,7 +403,7 @@ __global__ void __launch_bounds__(kMaxThreads, G >= 4 ? 2 : 1) resident_kernel(R
         double speed_acc = 0.0;
         unsigned long long ca = 0, cs = 0;
         Tally tally;
-        const AgentParams ap{a.R, a.dt, a.tau, a.tau_o, a.robot_alpha, a.K, a.segs, a.err};
+        const AgentParams ap{a.R, a.dt, a.tau, a.tau_o, a.robot_alpha, a.K, a.segs, a.err, a.seg_vd};
         // the queue capacity depends on this environment alone, so that its
         // results do not depend on the batch it runs in
         const FbQueue fbq{&s_fb_count, min(S.fb_cap, fb_capacity(c.n)), S.lmax, S.fb, S.fb_lines,

@@ -405,6 +405,7 @@ crowd_status crowd_server_tick(crowd_server_t s, int32_t* n_live, int32_t* n_fin
     a.tau_o = s->p.time_horizon_obst > 0.f ? s->p.time_horizon_obst : s->p.time_horizon;
     a.R = s->p.neighbor_dist;
     a.robot_alpha = s->p.robot_responsibility;
+    a.seg_vd = (s->p.flags & CROWD_FLAG_VELOCITY_SEGMENTS) ? 1 : 0;
     a.K = s->p.max_neighbors;
     const bool stats = (s->p.flags & CROWD_FLAG_STATS) != 0;
     a.stats = stats ? s->stats : nullptr;

@@ -287,7 +287,7 @@ __global__ void __launch_bounds__(kUpdateThreads) tiled_update(TiledStepArgs a) 
     }
     __syncthreads();
 
-    const AgentParams ap{a.R, a.dt, a.tau, a.tau_o, a.robot_alpha, a.K, a.segs, a.err};
+    const AgentParams ap{a.R, a.dt, a.tau, a.tau_o, a.robot_alpha, a.K, a.segs, a.err, a.seg_vd};
     Tally w;
     unsigned long long ca = 0, cs = 0;
     double speed = 0.0;

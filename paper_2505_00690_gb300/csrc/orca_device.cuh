@@ -407,6 +407,182 @@ __device__ __forceinline__ Line obstacle_line(float px, float py, float vx, floa
     return L;
 }
 
+// ---------------------------------------------------------------- A4v ---
+// Velocity-dependent half-plane against a static segment (full
+// responsibility): the tangent of the segment's truncated velocity obstacle
+// at its boundary point X nearest the current velocity v, (v' - X).n >= 0.
+// The obstacle is the capsule C = [a - p, b - p] + D(r); its truncated VO is
+// bounded by the two legs (rays from 0 tangent to C beyond the tangent
+// points) and by the part of C / tau_o that faces 0.  Candidates, each the
+// nearest point of one piece: the flat side of C / tau_o towards 0 (when it
+// faces 0), the end-cap arcs that face 0 (their radial point, when it lies
+// on the arc), and the two legs; the first of equally near pieces wins (flat,
+// cap a, cap b, left, right).  Overlapping (d <= r): as obstacle_line.  When
+// the two nearest pieces are within 2e-5 m/s, FP32 rounding could pick the
+// other one, so the choice is made again in FP64.
+
+// Unit tangent direction from 0 to the disk D(X, r) (left or right) and the
+// tangent length; gap2 = |X|^2 - r^2 (compensated by the caller).
+__device__ __forceinline__ void vd_leg(float x0, float x1, float r, float gap2, bool left, float& ux, float& uy,
+                                       float& len) {
+    const float l = sqrtf(fmaxf(gap2, 0.f));
+    const float inv = __frcp_fast(x0 * x0 + x1 * x1);
+    if (left) {
+        ux = (x0 * l - x1 * r) * inv;
+        uy = (x0 * r + x1 * l) * inv;
+    } else {
+        ux = (x0 * l + x1 * r) * inv;
+        uy = (-x0 * r + x1 * l) * inv;
+    }
+    len = l;
+}
+
+struct VdBest {
+    float best = INFINITY, second = INFINITY;
+    Line L{0.f, 0.f, 0.f, 0.f};
+    __device__ __forceinline__ void take(float dd, float x0, float x1, float n0, float n1) {
+        if (dd < best) {
+            second = best;
+            best = dd;
+            L = Line{x0, x1, n0, n1};
+        } else if (dd < second) {
+            second = dd;
+        }
+    }
+};
+
+static __device__ __noinline__ Line obstacle_line_vd_fp64(float px, float py, float vxf, float vyf, float rf,
+                                                          float4 s, float tau_of) {
+    const double vx = vxf, vy = vyf, r = rf, tau = tau_of;
+    const double A0 = (double)s.x - (double)px, A1 = (double)s.y - (double)py;
+    const double B0 = (double)s.z - (double)px, B1 = (double)s.w - (double)py;
+    double L0, L1, Ll, R0, R1, Rl;
+    {
+        double la[3], lb[3], ra[3], rb[3];
+        const double XA[2] = {A0, A1}, XB[2] = {B0, B1};
+        for (int k = 0; k < 4; ++k) {
+            const double* X = (k & 1) ? XB : XA;
+            const bool left = k < 2;
+            const double d2 = X[0] * X[0] + X[1] * X[1];
+            const double l = sqrt(fmax(d2 - r * r, 0.0));
+            double* o = left ? ((k & 1) ? lb : la) : ((k & 1) ? rb : ra);
+            o[0] = left ? (X[0] * l - X[1] * r) / d2 : (X[0] * l + X[1] * r) / d2;
+            o[1] = left ? (X[0] * r + X[1] * l) / d2 : (-X[0] * r + X[1] * l) / d2;
+            o[2] = l;
+        }
+        if (la[0] * lb[1] - la[1] * lb[0] > 0.0) { L0 = lb[0]; L1 = lb[1]; Ll = lb[2]; }
+        else { L0 = la[0]; L1 = la[1]; Ll = la[2]; }
+        if (ra[0] * rb[1] - ra[1] * rb[0] < 0.0) { R0 = rb[0]; R1 = rb[1]; Rl = rb[2]; }
+        else { R0 = ra[0]; R1 = ra[1]; Rl = ra[2]; }
+    }
+    double best = 1e300, X0 = 0.0, X1 = 0.0, N0 = 0.0, N1 = 0.0;
+    const double rt = r / tau;
+    const double a0 = A0 / tau, a1 = A1 / tau, b0 = B0 / tau, b1 = B1 / tau;
+    const double e0 = B0 - A0, e1 = B1 - A1, el = sqrt(e0 * e0 + e1 * e1);
+    if (el > 0.0) {
+        double m0 = -e1 / el, m1 = e0 / el;
+        if (m0 * A0 + m1 * A1 > 0.0) { m0 = -m0; m1 = -m1; }
+        if (m0 * A0 + m1 * A1 < -r) {
+            const double f0 = a0 + rt * m0, f1 = a1 + rt * m1, g0 = b0 - a0, g1 = b1 - a1;
+            double t = ((vx - f0) * g0 + (vy - f1) * g1) / (g0 * g0 + g1 * g1);
+            t = fmin(fmax(t, 0.0), 1.0);
+            const double x0 = f0 + t * g0, x1 = f1 + t * g1;
+            const double dd = sqrt((vx - x0) * (vx - x0) + (vy - x1) * (vy - x1));
+            if (dd < best) { best = dd; X0 = x0; X1 = x1; N0 = m0; N1 = m1; }
+        }
+    }
+    for (int cap = 0; cap < 2; ++cap) {
+        const double c0 = cap ? b0 : a0, c1 = cap ? b1 : a1;
+        const double o0 = cap ? A0 - B0 : B0 - A0, o1 = cap ? A1 - B1 : B1 - A1;
+        const double w0 = vx - c0, w1 = vy - c1, wl = sqrt(w0 * w0 + w1 * w1);
+        if (!(wl > 0.0)) continue;
+        const double u0 = w0 / wl, u1 = w1 / wl;
+        if (u0 * o0 + u1 * o1 > 0.0) continue;
+        if (!(u0 * c0 + u1 * c1 < -rt)) continue;
+        const double dd = fabs(wl - rt);
+        if (dd < best) { best = dd; X0 = c0 + rt * u0; X1 = c1 + rt * u1; N0 = u0; N1 = u1; }
+    }
+    {
+        const double t = fmax(vx * L0 + vy * L1, Ll / tau);
+        const double x0 = t * L0, x1 = t * L1;
+        const double dd = sqrt((vx - x0) * (vx - x0) + (vy - x1) * (vy - x1));
+        if (dd < best) { best = dd; X0 = x0; X1 = x1; N0 = -L1; N1 = L0; }
+    }
+    {
+        const double t = fmax(vx * R0 + vy * R1, Rl / tau);
+        const double x0 = t * R0, x1 = t * R1;
+        const double dd = sqrt((vx - x0) * (vx - x0) + (vy - x1) * (vy - x1));
+        if (dd < best) { best = dd; X0 = x0; X1 = x1; N0 = R1; N1 = -R0; }
+    }
+    return Line{(float)X0, (float)X1, (float)N0, (float)N1};
+}
+
+// Kept out of line: the default segment lines do not pay for its registers.
+static __device__ __noinline__ Line obstacle_line_vd(float px, float py, float vx, float vy, float r, float vmax,
+                                                     float4 s, float tau_o, float dt) {
+    float cx, cy;
+    if (!(seg_dist2(px, py, s, cx, cy) > r * r)) return obstacle_line(px, py, vx, vy, r, vmax, s, tau_o, dt);
+    const float A0 = s.x - px, A1 = s.y - py, B0 = s.z - px, B1 = s.w - py;
+    float L0, L1, Ll, R0, R1, Rl;
+    {
+        const float ga = contact_gap2(px, py, s.x, s.y, r, 0.f), gb = contact_gap2(px, py, s.z, s.w, r, 0.f);
+        float la0, la1, lal, lb0, lb1, lbl, ra0, ra1, ral, rb0, rb1, rbl;
+        vd_leg(A0, A1, r, ga, true, la0, la1, lal);
+        vd_leg(B0, B1, r, gb, true, lb0, lb1, lbl);
+        vd_leg(A0, A1, r, ga, false, ra0, ra1, ral);
+        vd_leg(B0, B1, r, gb, false, rb0, rb1, rbl);
+        const bool lb_out = la0 * lb1 - la1 * lb0 > 0.f, rb_out = ra0 * rb1 - ra1 * rb0 < 0.f;
+        L0 = lb_out ? lb0 : la0;
+        L1 = lb_out ? lb1 : la1;
+        Ll = lb_out ? lbl : lal;
+        R0 = rb_out ? rb0 : ra0;
+        R1 = rb_out ? rb1 : ra1;
+        Rl = rb_out ? rbl : ral;
+    }
+    const float inv_tau = __frcp_fast(tau_o);
+    const float rt = r * inv_tau;
+    const float a0 = A0 * inv_tau, a1 = A1 * inv_tau, b0 = B0 * inv_tau, b1 = B1 * inv_tau;
+    VdBest vb;
+    const float e0 = B0 - A0, e1 = B1 - A1, ee = e0 * e0 + e1 * e1;
+    if (ee > 0.f) {
+        const float ie = rsqrtf(ee);
+        float m0 = -e1 * ie, m1 = e0 * ie;
+        if (m0 * A0 + m1 * A1 > 0.f) {
+            m0 = -m0;
+            m1 = -m1;
+        }
+        if (m0 * A0 + m1 * A1 < -r) {
+            const float f0 = a0 + rt * m0, f1 = a1 + rt * m1, g0 = b0 - a0, g1 = b1 - a1;
+            const float t = fminf(fmaxf(((vx - f0) * g0 + (vy - f1) * g1) / (g0 * g0 + g1 * g1), 0.f), 1.f);
+            const float x0 = f0 + t * g0, x1 = f1 + t * g1;
+            vb.take(sqrtf((vx - x0) * (vx - x0) + (vy - x1) * (vy - x1)), x0, x1, m0, m1);
+        }
+    }
+#pragma unroll
+    for (int cap = 0; cap < 2; ++cap) {
+        const float c0 = cap ? b0 : a0, c1 = cap ? b1 : a1;
+        const float o0 = cap ? -e0 : e0, o1 = cap ? -e1 : e1;
+        const float w0 = vx - c0, w1 = vy - c1, wl = sqrtf(w0 * w0 + w1 * w1);
+        if (!(wl > 0.f)) continue;
+        const float iw = __frcp_fast(wl);
+        const float u0 = w0 * iw, u1 = w1 * iw;
+        if (u0 * o0 + u1 * o1 > 0.f || !(u0 * c0 + u1 * c1 < -rt)) continue;
+        vb.take(fabsf(wl - rt), c0 + rt * u0, c1 + rt * u1, u0, u1);
+    }
+    {
+        const float t = fmaxf(vx * L0 + vy * L1, Ll * inv_tau);
+        const float x0 = t * L0, x1 = t * L1;
+        vb.take(sqrtf((vx - x0) * (vx - x0) + (vy - x1) * (vy - x1)), x0, x1, -L1, L0);
+    }
+    {
+        const float t = fmaxf(vx * R0 + vy * R1, Rl * inv_tau);
+        const float x0 = t * R0, x1 = t * R1;
+        vb.take(sqrtf((vx - x0) * (vx - x0) + (vy - x1) * (vy - x1)), x0, x1, R1, -R0);
+    }
+    if (vb.second - vb.best <= 2e-5f) return obstacle_line_vd_fp64(px, py, vx, vy, r, s, tau_o);
+    return vb.L;
+}
+
 // ---------------------------------------------------------------- A5 ----
 // Slack of the FP32 interval tests, in m/s: an interval that comes out empty
 // by less than this (a line touching the speed disk, three lines through one

@@ -587,3 +587,60 @@ def test_goal_queue_multi_step_equals_single_steps():
     for st, gi in outs[1:]:
         assert np.array_equal(st, outs[0][0]) and np.array_equal(gi, outs[0][1])
     assert outs[0][1].sum() > 50
+
+
+# ----------------------------------------------------------------------------- velocity-dependent segment lines
+
+@pytest.mark.parametrize("which,flags", [("urban", 0), ("uneven", 0), ("urban", 8)])
+def test_velocity_segments_teacher_forced(which, flags):
+    """CROWD_FLAG_VELOCITY_SEGMENTS (segment half-planes tangent to the
+    segment VO at its point nearest the current velocity): the same contract."""
+    import dataclasses
+
+    sc = scenes.urban_block(5, n_envs=6, steps=100) if which == "urban" else scenes.uneven_batch(4, n_envs=10,
+                                                                                                  steps=40)
+    sc = dataclasses.replace(sc, segment_mode=1)
+    worst, mism, fb = teacher_forced(sc, sc.steps, flags=flags)
+    assert mism == 0
+    assert worst <= VEL_TOL, worst
+
+
+def test_velocity_segments_rollout_statistics():
+    """Mean speed, reach fraction and reach time of one rollout within 1 %; the
+    collision count, whose chaotic spread is wider with these segment lines
+    (a 1-ulp change of the start moves the oracle's own count by up to 1.5 %),
+    as the mean of three rollouts from 1-ulp perturbed starts, within 3 %."""
+    import dataclasses
+
+    from paper_2505_00690_gb300 import crowd as cw
+
+    base = dataclasses.replace(scenes.urban_block(0, n_envs=64, steps=300), segment_mode=1)
+    steps = base.steps
+    ped = np.ones(base.n_agents, bool)
+    for e in range(base.n_envs):
+        if base.robot_index[e] >= 0:
+            ped[base.env_start[e] + base.robot_index[e]] = False
+    coll_g, coll_o = [], []
+    for k in range(3):
+        sc = base
+        if k:
+            rng = np.random.default_rng(k)
+            up = rng.random(base.pos.shape) < 0.5
+            pos = np.where(up, np.nextafter(base.pos, np.float32(np.inf)), np.nextafter(base.pos, np.float32(-np.inf)))
+            sc = dataclasses.replace(base, pos=pos.astype(np.float32))
+        ref = oracle.rollout(sc, steps, threads=4)
+        cr = _crowd(sc, cw.CROWD_FLAG_STATS)
+        cr.step(sc.robot_vel[:steps], n_steps=steps)
+        env, reach = cr.stats()
+        cr.close()
+        coll_g.append(sum(s["agent_collisions"] + s["segment_collisions"] for s in env))
+        coll_o.append(ref["collisions"])
+        if k == 0:
+            mean_speed = sum(s["speed_sum"] for s in env) / (ped.sum() * steps)
+            reached = (reach > 0) & ped
+            mrt = reach[reached].mean() * float(np.float32(sc.dt))
+            assert _close(mean_speed, ref["mean_speed"])
+            assert _close(mrt, ref["mean_reach_time"])
+            assert abs(reached.sum() / ped.sum() - ref["reach_fraction"]) <= max(0.01, 1.0 / ped.sum())
+    print("collisions gpu", coll_g, "oracle", coll_o)
+    assert _close(float(np.mean(coll_g)), float(np.mean(coll_o)), rel=0.03)

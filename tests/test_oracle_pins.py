@@ -380,6 +380,21 @@ def test_velocity_segment_line_matches_vo_geometry(seed):
     assert np.allclose(n, n_bf, atol=1e-3), (n, n_bf)
 
 
+def test_velocity_segment_covered_at_polygon_vertex():
+    """A square's corner nearest the agent: the first edge's line (tangent at
+    the corner's cap, normal in the corner's normal cone) forbids both end
+    disks of the other edge's cutoff capsule, which then gets no line; an edge
+    facing away is not covered by a leg it does not lie behind."""
+    p, r, tau = np.array([0.0, 0.0]), 0.3, 2.0
+    e1 = (2.0, 2.0, 4.0, 2.0)   # bottom edge of the square [2,4] x [2,4]
+    e2 = (2.0, 2.0, 2.0, 4.0)   # left edge, sharing the corner (2, 2)
+    line1 = oracle.obstacle_line_vd(p, (0.0, 0.0), r, 1.5, e1, tau, 0.1)
+    assert np.allclose(line1[1], -np.array([1.0, 1.0]) / np.sqrt(2), atol=1e-12)  # the corner cap, towards 0
+    assert oracle.segment_covered(p, r, e2, tau, [line1])
+    far = (-6.0, -1.0, -6.0, 1.0)  # a segment on the other side
+    assert not oracle.segment_covered(p, r, far, tau, [line1])
+
+
 def test_velocity_segment_line_overlap_is_o4():
     for v in ((0.3, -0.2), (0.0, 0.0)):
         q1, n1 = oracle.obstacle_line_vd((0.0, 0.1), v, 0.3, 1.4, (-1.0, 0.0, 1.0, 0.0), 2.0, 0.1)
@@ -716,8 +731,15 @@ def _check_step_invariants(o, sc, pos, vel, robot_vel, nv, st):
             assert np.linalg.norm(nv[g]) <= vmax * (1 + 1e-12) + 1e-15
             ids, _ = oracle.neighbors(pos[base:base + n], i, R, K)
             oids = oracle.obstacles(segs, pos[g], float(sc.radius[g]) + tau_o * vmax) if len(segs) else []
-            seg_line = oracle.obstacle_line_vd if prm.seg_mode == 1 else oracle.obstacle_line
-            lines = [seg_line(pos[g], V[i], sc.radius[g], vmax, segs[s], tau_o, dt) for s in oids]
+            lines = []
+            for s in oids:
+                if prm.seg_mode == 1:
+                    if oracle.segment_covered(pos[g], sc.radius[g], segs[s], tau_o, lines):
+                        continue
+                    lines.append(oracle.obstacle_line_vd(pos[g], V[i], sc.radius[g], vmax, segs[s], tau_o, dt))
+                else:
+                    lines.append(oracle.obstacle_line(pos[g], V[i], sc.radius[g], vmax, segs[s], tau_o, dt))
+            n_hard = len(lines)
             for j in ids:
                 alpha = ra if j == robot else 0.5
                 lines.append(oracle.agent_line(pos[g], V[i], sc.radius[g], pos[base + j], V[j],
@@ -727,7 +749,7 @@ def _check_step_invariants(o, sc, pos, vel, robot_vel, nv, st):
                     assert (nv[g] - q) @ nrm >= -1e-9
             else:
                 assert st[g] == 1
-                hard = lines[:len(oids)]
+                hard = lines[:n_hard]
                 if brute_lp(hard, vmax, (0.0, 0.0)) is not None:
                     for q, nrm in hard:
                         assert (nv[g] - q) @ nrm >= -1e-9
