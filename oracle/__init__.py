@@ -81,7 +81,7 @@ def lib():
             L.or_lp2.restype = C.c_int
             L.or_fallback.argtypes = [C.POINTER(Line), C.c_int, C.c_int, d, d, d, pd, pd, pd]
             L.or_step.argtypes = [i32, pi64, pd, pd, pd, pi32, pi64, pd, C.POINTER(Params), pd, pd, pd, pd,
-                                  i64, pi64, pd, pd, pi32, pi32, C.c_int]
+                                  pi32, i64, pi64, pd, pd, pi32, pi32, C.c_int]
             L.or_step.restype = C.c_int
             L.or_collisions.argtypes = [i32, pi64, pd, pi64, pd, pd, pi64, pi64]
             _lib = L
@@ -253,11 +253,13 @@ class OracleScene:
         self.params = scene_params(scene)
         self.dt = self.params.dt
 
-    def step(self, pos, vel, robot_vel=None, sel=None, threads=1, goal=None):
-        """O1-O7 for the selected agents (all when sel is None).
+    def step(self, pos, vel, robot_vel=None, sel=None, threads=1, goal=None, kind=None):
+        """O1-O7 for the selected agents (all when sel is None).  `kind` [N]:
+        1 marks vehicles, which keep the given velocity (their lane model's).
 
         Returns (pos_out, vel_out, nbrs [N,K] env-local ids -1 padded, status [N]);
         rows of unselected agents are left as NaN / -9."""
+        kd = None if kind is None else np.ascontiguousarray(kind, np.int32)
         pos, vel = _f64(pos).reshape(-1, 2), _f64(vel).reshape(-1, 2)
         goal = self.goal if goal is None else _f64(goal).reshape(-1, 2)
         rv = _f64(np.zeros((self.E, 2)) if robot_vel is None else robot_vel).reshape(-1, 2)
@@ -274,6 +276,7 @@ class OracleScene:
                            _p(self.vmax, C.c_double), _p(self.pref, C.c_double), _p(self.robot, C.c_int32),
                            _p(self.seg_start, C.c_int64), _p(self.segs, C.c_double), C.byref(self.params),
                            _p(pos, C.c_double), _p(vel, C.c_double), _p(goal, C.c_double), _p(rv, C.c_double),
+                           None if kd is None else _p(kd, C.c_int32),
                            ns, sp, _p(po, C.c_double), _p(vo, C.c_double), _p(nb, C.c_int32),
                            _p(st, C.c_int32), int(threads))
         if rc != 0:

@@ -510,12 +510,15 @@ void or_fallback(const or_line* L, int n, int n_hard, double vmax, double prefx,
  * every other agent sees that commanded velocity.
  * Outputs (indexed by global agent id, only selected agents written):
  *   pos_out/vel_out [N][2]; nbr_out [N][K] env-local ids, -1 padded (may be
- *   NULL); status_out [N]: 0 LP feasible, 1 fallback, 2 robot (may be NULL).
+ *   NULL); status_out [N]: 0 LP feasible, 1 fallback, 2 robot, 3 vehicle (may be NULL).
+ * kind [N] (may be NULL): 1 marks a vehicle, which keeps its given velocity
+ * (set by its lane model) and which the others avoid with full
+ * responsibility. 
  * Returns 0, or -1 on bad arguments. */
 int or_step(int32_t n_envs, const int64_t* env_start, const double* radius, const double* vmax,
             const double* pref_speed, const int32_t* robot_index, const int64_t* seg_start,
             const double* segs, const or_params* prm, const double* pos, const double* vel,
-            const double* goal, const double* robot_vel, int64_t n_sel, const int64_t* sel,
+            const double* goal, const double* robot_vel, const int32_t* kind, int64_t n_sel, const int64_t* sel,
             double* pos_out, double* vel_out, int32_t* nbr_out, int32_t* status_out, int n_threads)
 {
     if (!prm || prm->max_neighbors < 0 || prm->max_neighbors > OR_MAX_K) return -1;
@@ -557,6 +560,10 @@ int or_step(int32_t n_envs, const int64_t* env_start, const double* radius, cons
         if (i == robot) {
             nvx = OR_VEL(i, 0); nvy = OR_VEL(i, 1);
             status = 2;
+        } else if (kind && kind[g] == 1) {
+            /* a vehicle: moved by its lane model, not solved */
+            nvx = OR_VEL(i, 0); nvy = OR_VEL(i, 1);
+            status = 3;
         } else {
             double prefx, prefy;
             or_pref_velocity(P[2 * i], P[2 * i + 1], goal[2 * g], goal[2 * g + 1], pref_speed[g],
@@ -582,7 +589,9 @@ int or_step(int32_t n_envs, const int64_t* env_start, const double* radius, cons
             no = kept;
             for (int k = 0; k < nn; ++k) {
                 int j = ids[k];
-                double alpha = (j == robot) ? prm->robot_alpha : 0.5;
+                /* half the avoidance against another agent, the robot's share
+                 * against the robot, all of it against a vehicle */
+                double alpha = (j == robot) ? prm->robot_alpha : (kind && kind[base + j] == 1) ? 1.0 : 0.5;
                 or_agent_line(P[2 * i], P[2 * i + 1], OR_VEL(i, 0), OR_VEL(i, 1), radius[g],
                               P[2 * j], P[2 * j + 1], OR_VEL(j, 0), OR_VEL(j, 1), radius[base + j],
                               prm->tau, prm->dt, alpha, i, j, &L[no + k]);

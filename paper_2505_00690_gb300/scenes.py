@@ -432,6 +432,69 @@ def goal_queue(scene: Scene, n_goals: int, seed: int = 0, hop: float | None = No
     return q
 
 
+@dataclass
+class Vehicles:
+    """Lane-following vehicles of a Scene (crowd_set_vehicles): closed lane
+    polylines, and per vehicle its agent slot (global index), lane, arc
+    position, speed and IDM parameters (v0, T, a, b, s0, length)."""
+
+    lane_start: np.ndarray  # int32 [n_lanes + 1]
+    points: np.ndarray      # float32 [P][2]
+    agent: np.ndarray       # int32 [V]
+    lane: np.ndarray        # int32 [V]
+    s: np.ndarray           # float32 [V]
+    v: np.ndarray           # float32 [V]
+    params: np.ndarray      # float32 [V][6]
+    half_width: float = 1.5
+    lookahead: float = 25.0
+
+
+def urban_block_with_vehicles(seed=0, n_envs=16, n_peds=96, n_vehicles=5, steps=300, **kw):
+    """Urban blocks with a one-lane ring road 3 m inside the block edge and
+    `n_vehicles` cars per block on it (equally spaced, speed U[0, 6] m/s,
+    desired speed U[8, 12] m/s, T 1.5 s, a 1.5 m/s^2, b 2 m/s^2, s0 2 m,
+    length 4.5 m; the crowd sees each car as an agent of radius 1.2 m).
+    Returns (Scene, Vehicles); the cars are the last agents of each env."""
+    base = urban_block(seed, n_envs=n_envs, n_peds=n_peds, steps=steps, **kw)
+    rng = np.random.Generator(np.random.PCG64(seed + 7919))
+    side = float(kw.get("side", 40.0))
+    envs, lane_pts, lane_start = [], [], [0]
+    agent, lane, s0, v0, params = [], [], [], [], []
+    total = 0
+    for e in range(base.n_envs):
+        a, b = int(base.env_start[e]), int(base.env_start[e + 1])
+        m = 3.0
+        ring = np.array([(m, m), (side - m, m), (side - m, side - m), (m, side - m)], np.float32)
+        lane_pts.append(ring)
+        lane_start.append(lane_start[-1] + len(ring))
+        L = 4 * (side - 2 * m)
+        offs = (np.arange(n_vehicles) + rng.uniform(0, 0.3)) * L / n_vehicles
+        pos = []
+        for k in range(n_vehicles):
+            sk = offs[k] % L
+            seg, t = int(sk // (side - 2 * m)), (sk % (side - 2 * m)) / (side - 2 * m)
+            pos.append(ring[seg] + t * (ring[(seg + 1) % 4] - ring[seg]))
+            agent.append(total + (b - a) + k)
+            lane.append(e)
+            s0.append(sk)
+            v0.append(rng.uniform(0.0, 6.0))
+            params.append((rng.uniform(8.0, 12.0), 1.5, 1.5, 2.0, 2.0, 4.5))
+        envs.append(dict(radius=np.concatenate([base.radius[a:b], np.full(n_vehicles, 1.2, np.float32)]),
+                         max_speed=np.concatenate([base.max_speed[a:b], np.full(n_vehicles, 12.0, np.float32)]),
+                         pref_speed=np.concatenate([base.pref_speed[a:b], np.zeros(n_vehicles, np.float32)]),
+                         pos=np.concatenate([base.pos[a:b], np.array(pos, np.float32)]),
+                         vel=np.concatenate([base.vel[a:b], np.zeros((n_vehicles, 2), np.float32)]),
+                         goal=np.concatenate([base.goal[a:b], np.array(pos, np.float32)]),
+                         segments=base.segments[base.seg_start[e]:base.seg_start[e + 1]],
+                         robot=int(base.robot_index[e])))
+        total += (b - a) + n_vehicles
+    sc = _pack(base.name + "+vehicles", envs, robot_vel=base.robot_vel, steps=steps)
+    veh = Vehicles(lane_start=np.array(lane_start, np.int32), points=np.concatenate(lane_pts).astype(np.float32),
+                   agent=np.array(agent, np.int32), lane=np.array(lane, np.int32),
+                   s=np.array(s0, np.float32), v=np.array(v0, np.float32), params=np.array(params, np.float32))
+    return sc, veh
+
+
 def make(name: str, seed: int = 0, **kw) -> Scene:
     return {"plain_square": plain_square, "urban_block": urban_block, "uneven_batch": uneven_batch,
             "dense_crowd": dense_crowd}[name](seed=seed, **kw)
