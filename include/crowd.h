@@ -165,6 +165,37 @@ crowd_status crowd_set_goal_queue(crowd_t h, int32_t n_goals, const float* goals
  * was set (0 without a queue).  Waits. */
 crowd_status crowd_read_goal_index(crowd_t h, int32_t* out);
 
+/* Lane-following vehicles (the paper's city scenes run cars beside the
+ * crowd under the Intelligent Driver Model of Treiber, Hennecke and Helbing,
+ * 2000).  Lanes are closed polylines: lane l has points
+ * points[lane_start[l]..lane_start[l+1]) ([P][2], at least 2, no zero-length
+ * segment; the last point joins the first).  Vehicle k (agents ascending) is
+ * crowd agent `agent[k]` (global index, not a robot slot, in an environment
+ * stepped by the shared-memory kernel, at most CROWD_MAX_VEHICLES_PER_ENV
+ * per environment), on lane `lane[k]` at arc position s[k] in [0, lane
+ * length) with speed v[k] >= 0, IDM parameters params[k][6] = (desired
+ * speed v0, time gap T, acceleration a, comfortable deceleration b, jam
+ * distance s0, length), all > 0.  Each step, from the step-start state, a
+ * car's leader is the nearest thing ahead on its lane: another car of the
+ * lane (gap ds - (len_i + len_j)/2, approach rate v_i - v_j) or a crowd agent
+ * within half_width + r of the lane and at most `lookahead` ahead (gap
+ * ds - len_i/2 - r, standing still); acceleration
+ * a (1 - (v/v0)^4 - (s_star / gap)^2), s_star = s0 + max(0, v T + v dv / (2 sqrt(a b))),
+ * the interaction term dropped with nothing ahead, the gap floored at
+ * 0.01 m; v' = max(0, v + acc dt), s' = s + v' dt (wrapped).  During the
+ * step the car is its agent at p(s) moving at (p(s') - p(s)) / dt; every
+ * other agent avoids it with full responsibility; it is left out of the
+ * speed and goal statistics and of goal queues.  n_vehicles = 0 removes the
+ * cars.  Copies everything; waits for the stream. */
+#define CROWD_MAX_VEHICLES_PER_ENV 32
+crowd_status crowd_set_vehicles(crowd_t h, int32_t n_lanes, const int32_t* lane_start, const float* points,
+                                int32_t n_vehicles, const int32_t* agent, const int32_t* lane, const float* s,
+                                const float* v, const float* params, float half_width, float lookahead);
+
+/* Arc positions s [V] and speeds v [V] of the vehicles: written from the host
+ * when `write` != 0 (s in [0, lane length), v >= 0), else read.  Waits. */
+crowd_status crowd_vehicle_state(crowd_t h, int32_t write, float* s, float* v);
+
 /* Full state [N][4] (px, py, vx, vy): resume from a checkpoint, or teacher
  * forcing from another simulator's state. */
 crowd_status crowd_set_state(crowd_t h, const float* state, int32_t ptr_kind);

@@ -30,7 +30,7 @@ EXPORTED = ["crowd_create", "crowd_set_goals", "crowd_set_state", "crowd_step", 
             "crowd_read_neighbors", "crowd_read_stats", "crowd_read_work", "crowd_reset_stats", "crowd_synchronize",
             "crowd_destroy", "crowd_num_agents", "crowd_num_envs", "crowd_last_error", "crowd_abi_version",
             "crowd_get_tuning", "crowd_set_tuning", "crowd_autotune", "crowd_set_goal_queue",
-            "crowd_read_goal_index"]
+            "crowd_read_goal_index", "crowd_set_vehicles", "crowd_vehicle_state"]
 
 
 class CrowdError(RuntimeError):
@@ -76,6 +76,8 @@ def load(path: str = LIB_PATH):
     L.crowd_set_goals.argtypes = [vp, vp, i32]
     L.crowd_set_goal_queue.argtypes = [vp, i32, vp, i32, i32]
     L.crowd_read_goal_index.argtypes = [vp, vp]
+    L.crowd_set_vehicles.argtypes = [vp, i32, vp, vp, i32, vp, vp, vp, vp, vp, C.c_float, C.c_float]
+    L.crowd_vehicle_state.argtypes = [vp, i32, vp, vp]
     L.crowd_set_state.argtypes = [vp, vp, i32]
     L.crowd_step.argtypes = [vp, C.c_float, vp, i32, i32]
     L.crowd_read_state.argtypes = [vp, vp, i32]
@@ -271,6 +273,29 @@ class Crowd:
         q = np.ascontiguousarray(queue, np.float32)
         assert q.ndim == 3 and q.shape[0] == self.N and q.shape[2] == 2
         _check(load().crowd_set_goal_queue(self.h, int(q.shape[1]), q.ctypes.data, int(bool(cyclic)), CROWD_HOST))
+
+    def set_vehicles(self, veh):
+        """Lane-following cars (scenes.Vehicles; see crowd_set_vehicles)."""
+        i32 = lambda a: np.ascontiguousarray(a, np.int32)
+        f32 = lambda a: np.ascontiguousarray(a, np.float32)
+        arrs = [i32(veh.lane_start), f32(veh.points), i32(veh.agent), i32(veh.lane), f32(veh.s), f32(veh.v),
+                f32(veh.params)]
+        self._veh_n = len(arrs[2])
+        _check(load().crowd_set_vehicles(self.h, len(arrs[0]) - 1, arrs[0].ctypes.data, arrs[1].ctypes.data,
+                                         self._veh_n, arrs[2].ctypes.data, arrs[3].ctypes.data, arrs[4].ctypes.data,
+                                         arrs[5].ctypes.data, arrs[6].ctypes.data, C.c_float(veh.half_width),
+                                         C.c_float(veh.lookahead)))
+
+    def vehicle_state(self):
+        n = getattr(self, "_veh_n", 0)
+        s, v = np.zeros(n, np.float32), np.zeros(n, np.float32)
+        if n:
+            _check(load().crowd_vehicle_state(self.h, 0, s.ctypes.data, v.ctypes.data))
+        return s, v
+
+    def set_vehicle_state(self, s, v):
+        s, v = np.ascontiguousarray(s, np.float32), np.ascontiguousarray(v, np.float32)
+        _check(load().crowd_vehicle_state(self.h, 1, s.ctypes.data, v.ctypes.data))
 
     def goal_index(self):
         out = np.zeros(self.N, np.int32)

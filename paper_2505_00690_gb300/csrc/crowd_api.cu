@@ -84,6 +84,21 @@ struct crowd_ctx {
     int* goal_idx = nullptr;       // [N]
     int goal_q = 0, goal_cyclic = 0;
     size_t goal_queue_cap = 0;     // entries allocated in goal_queue
+    // lane-following vehicles (crowd_set_vehicles)
+    int n_veh = 0;
+    int* veh_start = nullptr;      // [E + 1]
+    int* veh_agent = nullptr;      // [V]
+    int* veh_lane = nullptr;       // [V]
+    float* veh_s = nullptr;        // [V]
+    float* veh_v = nullptr;        // [V]
+    float4* veh_par_a = nullptr;   // [V]
+    float2* veh_par_b = nullptr;   // [V]
+    float2* lane_pts = nullptr;    // [P]
+    int* lane_start = nullptr;     // [n_lanes + 1]
+    float* lane_cum = nullptr;     // [P + n_lanes]
+    float veh_half_width = 0.f, veh_lookahead = 0.f;
+    std::vector<int> h_env_start;  // [E + 1] host copy
+    std::vector<char> h_env_tiled; // [E] environment stepped by the tiled path
     float4* segs = nullptr;
     float2* robot_vel = nullptr;
     size_t robot_vel_cap = 0;
@@ -128,6 +143,8 @@ struct crowd_ctx {
         if (graph) cudaGraphExecDestroy(graph);
         if (cap_stream) cudaStreamDestroy(cap_stream);
         void* ptrs[] = {env_start, seg_start, robot_index, order, queue, err, state, par, goal, goal_queue, goal_idx,
+                        veh_start, veh_agent, veh_lane, veh_s, veh_v, veh_par_a, veh_par_b, lane_pts, lane_start,
+                        lane_cum,
                         segs, robot_vel, nbr, reach, stats, work, tenvs, state_b, sorted_pv, key, rank,
                         count, start, sorted_id, seg_cell_start, seg_cell_ids, seg_grid, d_step};
         for (void* q : ptrs)
@@ -358,6 +375,8 @@ crowd_status resident_steps(crowd_t h, float dt, const float2* rv, int n_steps, 
     a.goal = h->goal;
     a.goals = GoalQueue{h->goal_queue, h->goal_idx, h->goal_q, h->goal_cyclic};
     a.seg_vd = (h->p.flags & CROWD_FLAG_VELOCITY_SEGMENTS) ? 1 : 0;
+    a.veh = VehicleArgs{h->n_veh, h->veh_start, h->veh_agent, h->veh_lane, h->veh_s, h->veh_v, h->veh_par_a,
+                        h->veh_par_b, h->lane_pts, h->lane_start, h->lane_cum, h->veh_half_width, h->veh_lookahead};
     a.state = h->state;
     a.robot_vel = rv;
     a.robot_stride = h->E;
@@ -582,9 +601,14 @@ crowd_status crowd_create(int32_t n_envs, const int32_t* agents_per_env, const f
     // so that its queue balances uneven batches); the others to the tiled path
     const bool force_tiled = (p->flags & CROWD_FLAG_FORCE_TILED) != 0;
     std::vector<int> order, tiled;
+    h->h_env_start = env_start;
+    h->h_env_tiled.assign(n_envs, 0);
     for (int e = 0; e < n_envs; ++e) {
         if (!force_tiled && agents_per_env[e] <= kResidentMaxAgents) order.push_back(e);
-        else tiled.push_back(e);
+        else {
+            tiled.push_back(e);
+            h->h_env_tiled[e] = 1;
+        }
     }
     std::stable_sort(order.begin(), order.end(),
                      [&](int a, int b) { return agents_per_env[a] > agents_per_env[b]; });
@@ -780,6 +804,155 @@ crowd_status crowd_set_goal_queue(crowd_t h, int32_t n_goals, const float* goals
     return CROWD_OK;
 }
 
+namespace {
+__global__ void mark_vehicles(float4* par, const int* agent, int n, float kind) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n) par[agent[k]].w = kind;
+}
+}  // namespace
+
+crowd_status crowd_set_vehicles(crowd_t h, int32_t n_lanes, const int32_t* lane_start, const float* points,
+                                int32_t n_vehicles, const int32_t* agent, const int32_t* lane, const float* s,
+                                const float* v, const float* params, float half_width, float lookahead) {
+    crowd_status st = check_handle(h);
+    if (st) return st;
+    if (n_vehicles < 0 || n_lanes < 0) return fail(CROWD_EINVAL, "n_vehicles and n_lanes must be >= 0");
+    if (n_vehicles > 0 && (!lane_start || !points || !agent || !lane || !s || !v || !params || n_lanes < 1))
+        return fail(CROWD_EINVAL, "vehicle arrays are null or no lane is given");
+    if (!(half_width >= 0.f) || !(lookahead > 0.f) || !std::isfinite(half_width) || !std::isfinite(lookahead))
+        return fail(CROWD_EINVAL, "half_width >= 0 and lookahead > 0 (finite) required");
+    // validate on the host
+    std::vector<double> cum;
+    std::vector<float> cumf;
+    int P = 0;
+    if (n_vehicles > 0) {
+        if (lane_start[0] != 0) return fail(CROWD_EINVAL, "lane_start[0] must be 0");
+        for (int l = 0; l < n_lanes; ++l)
+            if (lane_start[l + 1] - lane_start[l] < 2) return fail(CROWD_EINVAL, "lane %d has fewer than 2 points", l);
+        P = lane_start[n_lanes];
+        if (!finite_all(points, (size_t)P * 2)) return fail(CROWD_EINVAL, "lane points hold NaN/Inf");
+        for (int l = 0; l < n_lanes; ++l) {
+            const int p0 = lane_start[l], m = lane_start[l + 1] - p0;
+            double c = 0.0;
+            cum.push_back(0.0);
+            for (int k = 0; k < m; ++k) {
+                const int q = p0 + (k + 1 == m ? 0 : k + 1);
+                const double ex = (double)points[2 * q] - points[2 * (p0 + k)];
+                const double ey = (double)points[2 * q + 1] - points[2 * (p0 + k) + 1];
+                const double ln = std::sqrt(ex * ex + ey * ey);
+                if (!(ln > 0.0)) return fail(CROWD_EINVAL, "lane %d has a zero-length segment", l);
+                c += ln;
+                cum.push_back(c);
+            }
+        }
+        std::vector<int> per_env(h->E, 0);
+        for (int k = 0; k < n_vehicles; ++k) {
+            if (agent[k] < 0 || agent[k] >= h->N) return fail(CROWD_EINVAL, "vehicle %d: agent out of range", k);
+            if (k > 0 && agent[k] <= agent[k - 1]) return fail(CROWD_EINVAL, "vehicle agents must ascend");
+            if (lane[k] < 0 || lane[k] >= n_lanes) return fail(CROWD_EINVAL, "vehicle %d: lane out of range", k);
+            const int e = (int)(std::upper_bound(h->h_env_start.begin(), h->h_env_start.end(), agent[k]) -
+                                h->h_env_start.begin()) - 1;
+            if (h->h_env_tiled[e]) return fail(CROWD_EINVAL, "vehicle %d: its environment runs on the tiled path", k);
+            if (++per_env[e] > CROWD_MAX_VEHICLES_PER_ENV)
+                return fail(CROWD_EINVAL, "more than %d vehicles in environment %d", CROWD_MAX_VEHICLES_PER_ENV, e);
+            int32_t robot = -1;
+            CUDA_TRY(cudaMemcpy(&robot, h->robot_index + e, sizeof(int32_t), cudaMemcpyDeviceToHost), "read robot");
+            if (agent[k] - h->h_env_start[e] == robot) return fail(CROWD_EINVAL, "vehicle %d is the robot slot", k);
+            const double L = cum[lane_start[lane[k] + 1] + lane[k]];
+            const float* pr = params + 6 * k;
+            if (!(s[k] >= 0.f) || !(s[k] < L) || !(v[k] >= 0.f) || !std::isfinite(v[k]))
+                return fail(CROWD_EINVAL, "vehicle %d: s in [0, lane length) and v >= 0 required", k);
+            for (int q = 0; q < 6; ++q)
+                if (!(pr[q] > 0.f) || !std::isfinite(pr[q]))
+                    return fail(CROWD_EINVAL, "vehicle %d: parameters must be finite and > 0", k);
+        }
+        cumf.assign(cum.begin(), cum.end());
+    }
+    CUDA_TRY(cudaStreamSynchronize(h->stream), "synchronize");
+    // unmark the old cars, release the old arrays
+    if (h->n_veh > 0) {
+        mark_vehicles<<<(h->n_veh + 255) / 256, 256, 0, h->stream>>>(h->par, h->veh_agent, h->n_veh, 0.f);
+        CUDA_TRY(cudaGetLastError(), "unmark vehicles");
+        CUDA_TRY(cudaStreamSynchronize(h->stream), "synchronize");
+    }
+    void** olds[] = {(void**)&h->veh_start, (void**)&h->veh_agent, (void**)&h->veh_lane, (void**)&h->veh_s,
+                     (void**)&h->veh_v, (void**)&h->veh_par_a, (void**)&h->veh_par_b, (void**)&h->lane_pts,
+                     (void**)&h->lane_start, (void**)&h->lane_cum};
+    for (void** q : olds)
+        if (*q) {
+            cudaFree(*q);
+            *q = nullptr;
+        }
+    h->n_veh = 0;
+    if (n_vehicles == 0) return CROWD_OK;
+    std::vector<int> start(h->E + 1, 0);
+    for (int k = 0; k < n_vehicles; ++k) {
+        const int e = (int)(std::upper_bound(h->h_env_start.begin(), h->h_env_start.end(), agent[k]) -
+                            h->h_env_start.begin()) - 1;
+        ++start[e + 1];
+    }
+    for (int e = 0; e < h->E; ++e) start[e + 1] += start[e];
+    std::vector<float4> pa(n_vehicles);
+    std::vector<float2> pb(n_vehicles);
+    for (int k = 0; k < n_vehicles; ++k) {
+        const float* pr = params + 6 * k;
+        pa[k] = make_float4(pr[0], pr[1], pr[2], pr[3]);
+        pb[k] = make_float2(pr[4], pr[5]);
+    }
+    CUDA_TRY(dev_alloc(&h->veh_start, (size_t)h->E + 1), "allocate vehicles");
+    CUDA_TRY(dev_alloc(&h->veh_agent, (size_t)n_vehicles), "allocate vehicles");
+    CUDA_TRY(dev_alloc(&h->veh_lane, (size_t)n_vehicles), "allocate vehicles");
+    CUDA_TRY(dev_alloc(&h->veh_s, (size_t)n_vehicles), "allocate vehicles");
+    CUDA_TRY(dev_alloc(&h->veh_v, (size_t)n_vehicles), "allocate vehicles");
+    CUDA_TRY(dev_alloc(&h->veh_par_a, (size_t)n_vehicles), "allocate vehicles");
+    CUDA_TRY(dev_alloc(&h->veh_par_b, (size_t)n_vehicles), "allocate vehicles");
+    CUDA_TRY(dev_alloc(&h->lane_pts, (size_t)P), "allocate lanes");
+    CUDA_TRY(dev_alloc(&h->lane_start, (size_t)n_lanes + 1), "allocate lanes");
+    CUDA_TRY(dev_alloc(&h->lane_cum, cumf.size()), "allocate lanes");
+    struct Copy {
+        void* dst;
+        const void* src;
+        size_t bytes;
+    } copies[] = {{h->veh_start, start.data(), sizeof(int) * (h->E + 1)},
+                  {h->veh_agent, agent, sizeof(int) * n_vehicles},
+                  {h->veh_lane, lane, sizeof(int) * n_vehicles},
+                  {h->veh_s, s, sizeof(float) * n_vehicles},
+                  {h->veh_v, v, sizeof(float) * n_vehicles},
+                  {h->veh_par_a, pa.data(), sizeof(float4) * n_vehicles},
+                  {h->veh_par_b, pb.data(), sizeof(float2) * n_vehicles},
+                  {h->lane_pts, points, sizeof(float2) * P},
+                  {h->lane_start, lane_start, sizeof(int) * (n_lanes + 1)},
+                  {h->lane_cum, cumf.data(), sizeof(float) * cumf.size()}};
+    for (const Copy& c : copies) CUDA_TRY(cudaMemcpy(c.dst, c.src, c.bytes, cudaMemcpyHostToDevice), "copy vehicles");
+    mark_vehicles<<<(n_vehicles + 255) / 256, 256, 0, h->stream>>>(h->par, h->veh_agent, n_vehicles, 1.f);
+    CUDA_TRY(cudaGetLastError(), "mark vehicles");
+    CUDA_TRY(cudaStreamSynchronize(h->stream), "synchronize");
+    h->n_veh = n_vehicles;
+    h->veh_half_width = half_width;
+    h->veh_lookahead = lookahead;
+    return CROWD_OK;
+}
+
+crowd_status crowd_vehicle_state(crowd_t h, int32_t write, float* s, float* v) {
+    crowd_status st = check_handle(h);
+    if (st) return st;
+    if (h->n_veh == 0) return CROWD_OK;
+    if (!s || !v) return fail(CROWD_EINVAL, "s and v must not be null");
+    if (write) {
+        for (int k = 0; k < h->n_veh; ++k)
+            if (!(s[k] >= 0.f) || !(v[k] >= 0.f) || !std::isfinite(s[k]) || !std::isfinite(v[k]))
+                return fail(CROWD_EINVAL, "vehicle %d: s and v must be finite and >= 0", k);
+        CUDA_TRY(cudaStreamSynchronize(h->stream), "synchronize");
+        CUDA_TRY(cudaMemcpy(h->veh_s, s, sizeof(float) * h->n_veh, cudaMemcpyHostToDevice), "copy vehicle s");
+        CUDA_TRY(cudaMemcpy(h->veh_v, v, sizeof(float) * h->n_veh, cudaMemcpyHostToDevice), "copy vehicle v");
+    } else {
+        CUDA_TRY(cudaStreamSynchronize(h->stream), "synchronize");
+        CUDA_TRY(cudaMemcpy(s, h->veh_s, sizeof(float) * h->n_veh, cudaMemcpyDeviceToHost), "copy vehicle s");
+        CUDA_TRY(cudaMemcpy(v, h->veh_v, sizeof(float) * h->n_veh, cudaMemcpyDeviceToHost), "copy vehicle v");
+    }
+    return CROWD_OK;
+}
+
 crowd_status crowd_read_goal_index(crowd_t h, int32_t* out) {
     crowd_status st = check_handle(h);
     if (st) return st;
@@ -942,6 +1115,7 @@ crowd_status crowd_autotune(crowd_t h, float dt, int32_t n_steps, crowd_tuning* 
         int* saved_reach = nullptr;
         float2* saved_goal = nullptr;  // with a goal queue, trials move goals on
         int* saved_gidx = nullptr;
+        float* saved_veh = nullptr;    // with vehicles, trials move the cars: [s | v]
         WorkCount saved_work{};
         CUDA_TRY(dev_alloc(&saved, h->N), "autotune scratch");
         cudaError_t e = dev_alloc(&saved_stats, h->E);
@@ -952,12 +1126,23 @@ crowd_status crowd_autotune(crowd_t h, float dt, int32_t n_steps, crowd_tuning* 
             e = cudaMemcpyAsync(saved_goal, h->goal, sizeof(float2) * h->N, cudaMemcpyDeviceToDevice, h->stream);
         if (e == cudaSuccess && h->goal_q)
             e = cudaMemcpyAsync(saved_gidx, h->goal_idx, sizeof(int) * h->N, cudaMemcpyDeviceToDevice, h->stream);
+        if (e == cudaSuccess && h->n_veh) e = dev_alloc(&saved_veh, 2 * (size_t)h->n_veh);
+        if (e == cudaSuccess && h->n_veh)
+            e = cudaMemcpyAsync(saved_veh, h->veh_s, sizeof(float) * h->n_veh, cudaMemcpyDeviceToDevice, h->stream);
+        if (e == cudaSuccess && h->n_veh)
+            e = cudaMemcpyAsync(saved_veh + h->n_veh, h->veh_v, sizeof(float) * h->n_veh, cudaMemcpyDeviceToDevice,
+                                h->stream);
         auto restore_start = [&]() {
             cudaError_t r = cudaMemcpyAsync(h->state, saved, sizeof(float4) * h->N, cudaMemcpyDeviceToDevice, h->stream);
             if (r == cudaSuccess && h->goal_q)
                 r = cudaMemcpyAsync(h->goal, saved_goal, sizeof(float2) * h->N, cudaMemcpyDeviceToDevice, h->stream);
             if (r == cudaSuccess && h->goal_q)
                 r = cudaMemcpyAsync(h->goal_idx, saved_gidx, sizeof(int) * h->N, cudaMemcpyDeviceToDevice, h->stream);
+            if (r == cudaSuccess && h->n_veh)
+                r = cudaMemcpyAsync(h->veh_s, saved_veh, sizeof(float) * h->n_veh, cudaMemcpyDeviceToDevice, h->stream);
+            if (r == cudaSuccess && h->n_veh)
+                r = cudaMemcpyAsync(h->veh_v, saved_veh + h->n_veh, sizeof(float) * h->n_veh,
+                                    cudaMemcpyDeviceToDevice, h->stream);
             return r;
         };
         cudaEvent_t t0 = nullptr, t1 = nullptr;
@@ -1026,6 +1211,7 @@ crowd_status crowd_autotune(crowd_t h, float dt, int32_t n_steps, crowd_tuning* 
         if (saved_reach) cudaFree(saved_reach);
         if (saved_goal) cudaFree(saved_goal);
         if (saved_gidx) cudaFree(saved_gidx);
+        if (saved_veh) cudaFree(saved_veh);
         apply_tuning(h, e == cudaSuccess ? best : before);
         if (e != cudaSuccess) return cuda_fail(e, "autotune");
     }

@@ -340,7 +340,8 @@ __device__ __forceinline__ float2 group_solve(const Grp<G>& g, const AgentParams
         if (s < nb.cnt && ((no + s) & (G - 1)) == g.lane) {
             const int j = nb.id[s];
             const float4 o = ag.state(j);
-            const float alpha = (j == robot) ? a.robot_alpha : 0.5f;
+            // all of the avoidance against a vehicle, which does not react
+            const float alpha = (j == robot) ? a.robot_alpha : (ag.vehicle(j) ? 1.f : 0.5f);
             mine[(no + s) / G] = agent_line(me.x, me.y, me.z, me.w, pr.x, o.x, o.y, o.z, o.w, ag.radius(j), a.tau,
                                             a.dt, alpha, i < j);
         }

@@ -15,6 +15,22 @@ struct GoalQueue {
     int cyclic;           // 1: after the last goal the queue starts again
 };
 
+// Lane-following vehicles of a handle (see crowd_set_vehicles).
+struct VehicleArgs {
+    int n;                  // vehicles (0: none)
+    const int* start;       // [E + 1]: the vehicles of env e are [start[e], start[e + 1])
+    const int* agent;       // [V] global agent slot
+    const int* lane;        // [V]
+    float* s;               // [V] arc position on the lane (updated in place)
+    float* v;               // [V] speed (updated in place)
+    const float4* par_a;    // [V] (v0, T, a, b)
+    const float2* par_b;    // [V] (s0, length)
+    const float2* pts;      // [P] lane points
+    const int* lane_start;  // [n_lanes + 1]
+    const float* cum;       // [P + n_lanes] cumulative lengths; lane l's start at lane_start[l] + l
+    float half_width, lookahead;
+};
+
 // Device error word bits.
 enum : int {
     kErrObstacleOverflow = 1,  // an agent had more segments in reach than the line buffer holds
@@ -73,6 +89,7 @@ struct ResidentArgs {
     const float4* par;      // [N] (radius, v_max, preferred speed, 0)
     float2* goal;           // [N] current goals (advanced in place with a goal queue)
     GoalQueue goals;        // goal queue (q = 0: none)
+    VehicleArgs veh;        // lane-following vehicles (n = 0: none)
     float4* state;          // [N] (px, py, vx, vy)
     const float2* robot_vel;  // [n_steps][robot_stride] or null (keep current)
     int robot_stride;       // entries per step in robot_vel (normally E)

@@ -644,3 +644,105 @@ def test_velocity_segments_rollout_statistics():
             assert abs(reached.sum() / ped.sum() - ref["reach_fraction"]) <= max(0.01, 1.0 / ped.sum())
     print("collisions gpu", coll_g, "oracle", coll_o)
     assert _close(float(np.mean(coll_g)), float(np.mean(coll_o)), rel=0.03)
+
+
+# ----------------------------------------------------------------------------- lane-following vehicles
+
+def _vehicle_kind(sc, veh):
+    kind = np.zeros(sc.n_agents, np.int32)
+    kind[veh.agent] = 1
+    return kind
+
+
+def _vehicle_oracle_step(sc, veh, lanes, S, vs, vv):
+    """Cars of every env from the teacher state: new (s, v) and the state rows
+    the crowd step starts from (position p(s), velocity (p(s') - p(s))/dt)."""
+    from oracle import vehicles as VH
+
+    S = S.copy()
+    s_new, v_new = vs.astype(np.float64).copy(), vv.astype(np.float64).copy()
+    kind = _vehicle_kind(sc, veh)
+    for e in range(sc.n_envs):
+        a, b = sc.env_start[e], sc.env_start[e + 1]
+        ks = np.nonzero((veh.agent >= a) & (veh.agent < b))[0]
+        if len(ks) == 0:
+            continue
+        blockers = kind[a:b] == 0
+        sn, vn, p_now, p_next, vel = VH.idm_step(lanes, veh.lane[ks], vs[ks], vv[ks], veh.params[ks], S[a:b, :2],
+                                                 sc.radius[a:b], blockers, veh.half_width, veh.lookahead,
+                                                 float(np.float32(sc.dt)))
+        s_new[ks], v_new[ks] = sn, vn
+        S[veh.agent[ks], :2] = p_now
+        S[veh.agent[ks], 2:] = vel
+    return s_new, v_new, S
+
+
+def test_vehicles_teacher_forced():
+    """Urban blocks with ring-road cars: the host runs the cars' IDM and the
+    crowd step of the oracle from the teacher state (cars as vehicles), the
+    GPU does both inside its step; car arc positions and speeds, pedestrian
+    velocities (1e-4) and neighbour lists (bit-exact) agree."""
+    from oracle import vehicles as VH
+    from paper_2505_00690_gb300 import crowd as cw
+
+    sc, veh = scenes.urban_block_with_vehicles(2, n_envs=6, n_peds=96, n_vehicles=5, steps=120)
+    lanes = VH.Lanes(veh.points, veh.lane_start)
+    kind = _vehicle_kind(sc, veh)
+    cr = _crowd(sc, cw.CROWD_FLAG_EXPORT_NEIGHBORS)
+    cr.set_vehicles(veh)
+    o = oracle.OracleScene(sc)
+    S = sc.state().astype(np.float32)
+    vs, vv = veh.s.copy(), veh.v.copy()
+    worst_ped, worst_car, mism, stopped = 0.0, 0.0, 0, 0
+    for k in range(sc.steps):
+        rv = sc.robot_vel_at(k).astype(np.float32)
+        s_new, v_new, S_start = _vehicle_oracle_step(sc, veh, lanes, S, vs, vv)
+        cr.set_state(S)
+        cr.set_vehicle_state(vs, vv)
+        cr.step(rv[None], n_steps=1)
+        G = cr.state()
+        gs, gv = cr.vehicle_state()
+        po, vo, nb, st = o.step(S_start[:, :2], S_start[:, 2:], rv, kind=kind)
+        assert np.all(st[veh.agent] == 3)
+        mism += int(np.any(cr.neighbors() != nb, axis=1).sum())
+        ped = kind == 0
+        worst_ped = max(worst_ped, float(np.abs(G[ped, 2:] - vo[ped]).max()))
+        L = np.array([lanes.length(int(l)) for l in veh.lane])
+        ds = (gs - s_new + 0.5 * L) % L - 0.5 * L  # arc difference on the ring
+        worst_car = max(worst_car, float(np.abs(gv - v_new).max()), float(np.abs(ds).max()) / float(np.float32(sc.dt)))
+        stopped += int((v_new < 0.05).sum())
+        S = np.concatenate([po, vo], 1).astype(np.float32)
+        vs, vv = s_new.astype(np.float32), v_new.astype(np.float32)
+    cr.close()
+    assert mism == 0
+    assert worst_ped <= VEL_TOL, worst_ped
+    assert worst_car <= VEL_TOL, worst_car
+    assert stopped > 0  # some cars had to stop for pedestrians on the road
+
+
+def test_vehicles_multi_step_equals_single_steps_and_autotune_restores():
+    from paper_2505_00690_gb300 import crowd as cw
+
+    sc, veh = scenes.urban_block_with_vehicles(3, n_envs=8, n_peds=64, n_vehicles=4, steps=60)
+    outs = []
+    for chunks in ((60,), (1,) * 60, (25, 35)):
+        cr = cw.Crowd(sc)
+        cr.set_vehicles(veh)
+        k = 0
+        for n in chunks:
+            cr.step(sc.robot_vel[k:k + n], n_steps=n)
+            k += n
+        outs.append((cr.state(), *cr.vehicle_state()))
+        cr.close()
+    for st, s, v in outs[1:]:
+        assert np.array_equal(st, outs[0][0]) and np.array_equal(s, outs[0][1]) and np.array_equal(v, outs[0][2])
+    cr = cw.Crowd(sc)
+    cr.set_vehicles(veh)
+    before = (cr.state(), *cr.vehicle_state())
+    cr.autotune(n_steps=10)
+    after = (cr.state(), *cr.vehicle_state())
+    assert all(np.array_equal(x, y) for x, y in zip(before, after))
+    with pytest.raises(cw.CrowdError):
+        bad = scenes.Vehicles(**{**veh.__dict__, "agent": veh.agent[::-1].copy()})
+        cr.set_vehicles(bad)
+    cr.close()
