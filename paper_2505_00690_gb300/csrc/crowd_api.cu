@@ -91,6 +91,7 @@ struct crowd_ctx {
     int* veh_lane = nullptr;       // [V]
     float* veh_s = nullptr;        // [V]
     float* veh_v = nullptr;        // [V]
+    float* veh_pref = nullptr;     // [V] preferred speeds of the car agents before they became cars
     float4* veh_par_a = nullptr;   // [V]
     float2* veh_par_b = nullptr;   // [V]
     float2* lane_pts = nullptr;    // [P]
@@ -144,7 +145,7 @@ struct crowd_ctx {
         if (cap_stream) cudaStreamDestroy(cap_stream);
         void* ptrs[] = {env_start, seg_start, robot_index, order, queue, err, state, par, goal, goal_queue, goal_idx,
                         veh_start, veh_agent, veh_lane, veh_s, veh_v, veh_par_a, veh_par_b, lane_pts, lane_start,
-                        lane_cum,
+                        lane_cum, veh_pref,
                         segs, robot_vel, nbr, reach, stats, work, tenvs, state_b, sorted_pv, key, rank,
                         count, start, sorted_id, seg_cell_start, seg_cell_ids, seg_grid, d_step};
         for (void* q : ptrs)
@@ -805,9 +806,20 @@ crowd_status crowd_set_goal_queue(crowd_t h, int32_t n_goals, const float* goals
 }
 
 namespace {
-__global__ void mark_vehicles(float4* par, const int* agent, int n, float kind) {
+// A car's agent carries w = 1 and a negative preferred speed (the kernels
+// test the sign of the value they hold anyway); `saved` keeps the speed.
+__global__ void mark_vehicles(float4* par, const int* agent, int n, int mark, float* saved) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k < n) par[agent[k]].w = kind;
+    if (k >= n) return;
+    float4& p = par[agent[k]];
+    if (mark) {
+        saved[k] = p.z;
+        p.z = -1.f;
+        p.w = 1.f;
+    } else {
+        p.z = saved[k];
+        p.w = 0.f;
+    }
 }
 }  // namespace
 
@@ -871,13 +883,13 @@ crowd_status crowd_set_vehicles(crowd_t h, int32_t n_lanes, const int32_t* lane_
     CUDA_TRY(cudaStreamSynchronize(h->stream), "synchronize");
     // unmark the old cars, release the old arrays
     if (h->n_veh > 0) {
-        mark_vehicles<<<(h->n_veh + 255) / 256, 256, 0, h->stream>>>(h->par, h->veh_agent, h->n_veh, 0.f);
+        mark_vehicles<<<(h->n_veh + 255) / 256, 256, 0, h->stream>>>(h->par, h->veh_agent, h->n_veh, 0, h->veh_pref);
         CUDA_TRY(cudaGetLastError(), "unmark vehicles");
         CUDA_TRY(cudaStreamSynchronize(h->stream), "synchronize");
     }
     void** olds[] = {(void**)&h->veh_start, (void**)&h->veh_agent, (void**)&h->veh_lane, (void**)&h->veh_s,
                      (void**)&h->veh_v, (void**)&h->veh_par_a, (void**)&h->veh_par_b, (void**)&h->lane_pts,
-                     (void**)&h->lane_start, (void**)&h->lane_cum};
+                     (void**)&h->lane_start, (void**)&h->lane_cum, (void**)&h->veh_pref};
     for (void** q : olds)
         if (*q) {
             cudaFree(*q);
@@ -909,6 +921,7 @@ crowd_status crowd_set_vehicles(crowd_t h, int32_t n_lanes, const int32_t* lane_
     CUDA_TRY(dev_alloc(&h->lane_pts, (size_t)P), "allocate lanes");
     CUDA_TRY(dev_alloc(&h->lane_start, (size_t)n_lanes + 1), "allocate lanes");
     CUDA_TRY(dev_alloc(&h->lane_cum, cumf.size()), "allocate lanes");
+    CUDA_TRY(dev_alloc(&h->veh_pref, (size_t)n_vehicles), "allocate vehicles");
     struct Copy {
         void* dst;
         const void* src;
@@ -924,7 +937,7 @@ crowd_status crowd_set_vehicles(crowd_t h, int32_t n_lanes, const int32_t* lane_
                   {h->lane_start, lane_start, sizeof(int) * (n_lanes + 1)},
                   {h->lane_cum, cumf.data(), sizeof(float) * cumf.size()}};
     for (const Copy& c : copies) CUDA_TRY(cudaMemcpy(c.dst, c.src, c.bytes, cudaMemcpyHostToDevice), "copy vehicles");
-    mark_vehicles<<<(n_vehicles + 255) / 256, 256, 0, h->stream>>>(h->par, h->veh_agent, n_vehicles, 1.f);
+    mark_vehicles<<<(n_vehicles + 255) / 256, 256, 0, h->stream>>>(h->par, h->veh_agent, n_vehicles, 1, h->veh_pref);
     CUDA_TRY(cudaGetLastError(), "mark vehicles");
     CUDA_TRY(cudaStreamSynchronize(h->stream), "synchronize");
     h->n_veh = n_vehicles;

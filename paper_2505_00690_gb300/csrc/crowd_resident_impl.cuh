@@ -234,7 +234,7 @@ __device__ __forceinline__ void integrate(const ResidentArgs& a, const Smem& S, 
     nx.z = v.x;
     nx.w = v.y;
     S.nv[i] = nx;
-    if (a.stats && i != c.robot && S.par[i].w == 0.f) {
+    if (a.stats && i != c.robot && S.par[i].z >= 0.f) {
         speed_acc += (double)sqrtf(v.x * v.x + v.y * v.y);
         if (a.reach) {
             int* rp = a.reach + c.base + i;
@@ -272,7 +272,7 @@ __device__ __forceinline__ bool agent_update(const ResidentArgs& a, const AgentP
     // A3-A5 (the robot is not solved: it keeps its command); an infeasible
     // LP is queued for the warp-cooperative fallback, integrated there
     ++w.agent_steps;
-    if (i == c.robot || pr.w != 0.f) {  // the robot and the cars move as commanded
+    if (i == c.robot) {
         integrate(a, S, c, i, me, pr.x, make_float2(me.z, me.w), speed_acc);
         return false;
     }
@@ -325,8 +325,8 @@ __device__ __forceinline__ bool lane_blocker(float2 q, float r, float2 a, float2
 // the lane's corridor and `lookahead`, sets the interaction term of
 // a (1 - (v/v0)^4 - (s*/gap)^2), s* = s0 + max(0, v T + v dv / (2 sqrt(a b)));
 // v' = max(0, v + acc dt), s' = s + v' dt wrapped onto the lane.
-__device__ __forceinline__ void idm_vehicle(const VehicleArgs& V, int vi, int v_begin, int v_end, const Smem& S, int n,
-                                            float dt, float& s_new, float& v_new) {
+__device__ __forceinline__ void idm_vehicle(const VehicleArgs& V, int vi, int v_begin, int v_end, const Smem& S,
+                                            int n, float dt, float& s_new, float& v_new) {
     const int l = V.lane[vi];
     const int p0 = V.lane_start[l], m = V.lane_start[l + 1] - p0;
     const float* cum = V.cum + p0 + l;
@@ -384,6 +384,40 @@ __device__ __forceinline__ void idm_vehicle(const VehicleArgs& V, int vi, int v_
     if (s_new >= L) s_new -= L;
 }
 
+// Commit the step of car vi: its arc state, and its agent row (position p(s),
+// velocity (p(s') - p(s)) / dt).
+__device__ __forceinline__ void place_vehicle(const VehicleArgs& V, int vi, float s_new, float v_new, float dt,
+                                                  float4* row) {
+    const int l = V.lane[vi];
+    const float2 p_now = lane_point(V, l, V.s[vi]), p_next = lane_point(V, l, s_new);
+    V.s[vi] = s_new;
+    V.v[vi] = v_new;
+    const float inv_dt = 1.f / dt;
+    *row = make_float4(p_now.x, p_now.y, (p_next.x - p_now.x) * inv_dt, (p_next.y - p_now.y) * inv_dt);
+}
+
+// A car's slot in the agent pass (cars are dispatched here by the kernel, so
+// that the agent update itself carries no test for them, which measurably
+// slowed it): the car's neighbour list when the lists are exported this
+// step, then the move of its commanded velocity.
+template <int KMAX>
+__device__ __noinline__ void vehicle_update(const ResidentArgs& a, const Smem& S, const StepCtx& c, int t,
+                                            double& speed_acc, Tally& w) {
+    const int i = S.sid[t];
+    const float4 me = S.spv[t];
+    if (c.last && a.nbr_out) {
+        NbList<KMAX> nb;
+        const SmemSource src{S.spv, S.sid, S.cell, c.g.W};
+        select_neighbors<KMAX>(src, cell_coord(me.x, c.g.x0, c.g.inv_c, c.g.W),
+                               cell_coord(me.y, c.g.y0, c.g.inv_c, c.g.H), c.g.W, c.g.H, i, me, a.R, a.K, nb, w,
+                               a.cell_split);
+        int* out = a.nbr_out + (size_t)(c.base + i) * a.K;
+        for (int s = 0; s < a.K; ++s) out[s] = s < nb.cnt ? nb.id[s] : -1;
+    }
+    ++w.agent_steps;
+    integrate(a, S, c, i, me, S.par[i].x, make_float2(me.z, me.w), speed_acc);
+}
+
 // One agent by a group of G lanes (see crowd_group.cuh); lane 0 writes.
 template <int KMAX, int G>
 __device__ __forceinline__ void agent_update_group(const ResidentArgs& a, const AgentParams& ap, const Smem& S,
@@ -405,7 +439,7 @@ __device__ __forceinline__ void agent_update_group(const ResidentArgs& a, const 
                 if (s < a.K) out[s] = s < nb.cnt ? nb.id[s] : -1;
         }
     }
-    if (i == c.robot || pr.w != 0.f) {
+    if (i == c.robot || pr.z < 0.f) {
         if (g.lane == 0) integrate(a, S, c, i, me, pr.x, make_float2(me.z, me.w), speed_acc);
         return;
     }
@@ -531,15 +565,7 @@ __global__ void __launch_bounds__(kMaxThreads, G >= 4 ? 2 : 1) resident_kernel(R
                 float s_new = 0.f, v_new = 0.f;
                 if (vi < ve) idm_vehicle(a.veh, vi, vb, ve, S, c.n, a.dt, s_new, v_new);
                 __syncthreads();
-                if (vi < ve) {
-                    const int l = a.veh.lane[vi];
-                    const float2 p_now = lane_point(a.veh, l, a.veh.s[vi]), p_next = lane_point(a.veh, l, s_new);
-                    a.veh.s[vi] = s_new;
-                    a.veh.v[vi] = v_new;
-                    const float inv_dt = 1.f / a.dt;
-                    S.pv[a.veh.agent[vi] - c.base] = make_float4(p_now.x, p_now.y, (p_next.x - p_now.x) * inv_dt,
-                                                                 (p_next.y - p_now.y) * inv_dt);
-                }
+                if (vi < ve) place_vehicle(a.veh, vi, s_new, v_new, a.dt, S.pv + (a.veh.agent[vi] - c.base));
             }
             if (compute && c.robot >= 0 && c.robot < c.n && a.robot_vel && threadIdx.x == 0) {
                 const size_t at = a.env_step0 ? (size_t)c.e * a.rv_env_stride + step0 + step
@@ -571,6 +597,11 @@ __global__ void __launch_bounds__(kMaxThreads, G >= 4 ? 2 : 1) resident_kernel(R
                 for (int b = 0; b < c.n; b += blockDim.x) {
                     const int t = b + (a.agent_order ? (threadIdx.x & 31) * warps + (threadIdx.x >> 5) : threadIdx.x);
                     if (t >= c.n) continue;
+                    if (S.par[S.sid[t]].z < 0.f) {  // a car (negative preferred speed)
+                        vehicle_update<KMAX>(a, S, c, t, speed_acc, tally);
+                        S.pend[t] = 0;
+                        continue;
+                    }
                     const bool def = agent_update<KMAX>(a, ap, S, c, t, speed_acc, tally, fbq, true);
                     S.pend[t] = def ? 1 : 0;
                     if (def) atomicAdd(&s_pend, 1);

@@ -151,9 +151,9 @@ __device__ __forceinline__ float contact_gap2(float pix, float piy, float pjx, f
     two_sum(pjx, -pix, xh, xl);
     two_sum(pjy, -piy, yh, yl);
     two_sum(ri, rj, rh, rl);
-    const float h1 = xh * xh, l1 = fmaf(xh, xh, -h1) + 2.f * xh * xl;
-    const float h2 = yh * yh, l2 = fmaf(yh, yh, -h2) + 2.f * yh * yl;
-    const float h3 = rh * rh, l3 = fmaf(rh, rh, -h3) + 2.f * rh * rl;
+    const float h1 = __fmul_rn(xh, xh), l1 = fmaf(xh, xh, -h1) + 2.f * xh * xl;
+    const float h2 = __fmul_rn(yh, yh), l2 = fmaf(yh, yh, -h2) + 2.f * yh * yl;
+    const float h3 = __fmul_rn(rh, rh), l3 = fmaf(rh, rh, -h3) + 2.f * rh * rl;
     float s, e1, t, e2;
     two_sum(h1, h2, s, e1);
     two_sum(s, -h3, t, e2);
@@ -596,10 +596,22 @@ constexpr float kTangentDisc = 2e-6f;
 // |det(n_k, n_l)| at or below which two lines count as parallel.
 constexpr float kEpsParallelF = 1e-9f;
 
-// p + e = a * b exactly (the FMA gives the rounding error of the product).
+// p + e = a * b exactly (the FMA gives the rounding error of the product;
+// p is rounded on its own, never fused into the sum that consumes it).
 __device__ __forceinline__ void two_prod(float a, float b, float& p, float& e) {
-    p = a * b;
+    p = __fmul_rn(a, b);
     e = fmaf(a, b, -p);
+}
+
+// The LP below writes every a*b + c*d as fma(a, b, round(c*d)) and every
+// q + t*d as one FMA.  Left to itself the compiler picks which product of a
+// sum to fuse from the code around it, so two inlined copies of the same LP
+// (the fallback run in place and the one run later from the queue) could
+// round differently; with the pattern fixed they give the same bits.
+__device__ __forceinline__ float fdot2(float a, float b, float c, float d) { return __fmaf_rn(a, b, __fmul_rn(c, d)); }
+// (v - q).n for a point v and a line through q with normal n
+__device__ __forceinline__ float side_of(float vx, float vy, float qx, float qy, float nx, float ny) {
+    return fdot2(vx - qx, nx, vy - qy, ny);
 }
 
 // Clip [lo, hi] on line k by a line l nearly parallel to it (|det| < 1e-4 in
@@ -624,7 +636,7 @@ __device__ __forceinline__ bool clip_near_parallel(const Line& lk, const Line& l
     two_prod(ax, ll.nx, q1, f1);
     two_prod(ay, ll.ny, q2, f2);
     two_sum(q1, q2, num, f3);
-    num += ((f1 + f2) + f3) + (axe * ll.nx + aye * ll.ny);
+    num += ((f1 + f2) + f3) + fdot2(axe, ll.nx, aye, ll.ny);
     if (fabsf(den) <= kEpsParallelF) return num > 0.f;
     const float t = num / den;
     if (den > 0.f) lo = fmaxf(lo, t);
@@ -639,8 +651,8 @@ __device__ __forceinline__ bool clip_near_parallel(const Line& lk, const Line& l
 __device__ __forceinline__ bool line_interval(const Line* L, int k, float vmax, float& tl, float& tr) {
     const Line lk = L[k];
     const float dx = -lk.ny, dy = lk.nx;
-    const float qd = lk.qx * dx + lk.qy * dy;
-    float disc = qd * qd - (lk.qx * lk.qx + lk.qy * lk.qy) + vmax * vmax;
+    const float qd = fdot2(lk.qx, dx, lk.qy, dy);
+    float disc = __fadd_rn(__fmaf_rn(qd, qd, -fdot2(lk.qx, lk.qx, lk.qy, lk.qy)), __fmul_rn(vmax, vmax));
     if (disc < 0.f) {
         // the line misses the disk by about -disc / (2 vmax)
         if (disc < -2.f * kIntervalSlack * vmax) return false;
@@ -659,8 +671,8 @@ __device__ __forceinline__ bool line_interval(const Line* L, int k, float vmax, 
     for (int l = 0; l < k; ++l) {
         const Line ll = nxt;
         if (l + 1 < k) nxt = L[l + 1];
-        const float den = dx * ll.nx + dy * ll.ny;  // det(n_k, n_l)
-        const float num = (ll.qx - lk.qx) * ll.nx + (ll.qy - lk.qy) * ll.ny;
+        const float den = fdot2(dx, ll.nx, dy, ll.ny);  // det(n_k, n_l)
+        const float num = side_of(ll.qx, ll.qy, lk.qx, lk.qy, ll.nx, ll.ny);
         if (fabsf(den) < 1e-4f) {
             if (clip_near_parallel(lk, ll, tl, tr)) return false;
         } else {
@@ -682,10 +694,10 @@ __device__ __forceinline__ bool lp1(const Line* L, int k, float vmax, float2 pre
     if (!line_interval(L, k, vmax, tl, tr)) return false;
     const Line lk = L[k];
     const float dx = -lk.ny, dy = lk.nx;
-    float t = (pref.x - lk.qx) * dx + (pref.y - lk.qy) * dy;
+    float t = side_of(pref.x, pref.y, lk.qx, lk.qy, dx, dy);
     t = fminf(fmaxf(t, tl), tr);
-    v.x = lk.qx + t * dx;
-    v.y = lk.qy + t * dy;
+    v.x = __fmaf_rn(t, dx, lk.qx);
+    v.y = __fmaf_rn(t, dy, lk.qy);
     return true;
 }
 
@@ -694,8 +706,8 @@ __device__ __forceinline__ bool lp1(const Line* L, int k, float vmax, float2 pre
 // they scan.
 __device__ __forceinline__ int lp2(const Line* L, int n, float vmax, float2 pref, float2& v, int& solves,
                                    int& solve_lines) {
-    const float pl2 = pref.x * pref.x + pref.y * pref.y;
-    if (pl2 > vmax * vmax) {
+    const float pl2 = fdot2(pref.x, pref.x, pref.y, pref.y);
+    if (pl2 > __fmul_rn(vmax, vmax)) {
         const float k = vmax * rsqrtf(pl2);
         v = make_float2(pref.x * k, pref.y * k);
     } else {
@@ -705,7 +717,7 @@ __device__ __forceinline__ int lp2(const Line* L, int n, float vmax, float2 pref
     for (int k = 0; k < n; ++k) {
         const Line lk = nxt;
         if (k + 1 < n) nxt = L[k + 1];
-        if ((v.x - lk.qx) * lk.nx + (v.y - lk.qy) * lk.ny < 0.f) {
+        if (side_of(v.x, v.y, lk.qx, lk.qy, lk.nx, lk.ny) < 0.f) {
             float2 nv;
             ++solves;
             solve_lines += k;
@@ -725,17 +737,17 @@ __device__ __forceinline__ bool lp_dir(const Line* S, int m, float vmax, float o
     v = make_float2(vmax * ox, vmax * oy);
     for (int k = 0; k < m; ++k) {
         const Line lk = S[k];
-        if ((v.x - lk.qx) * lk.nx + (v.y - lk.qy) * lk.ny < 0.f) {
+        if (side_of(v.x, v.y, lk.qx, lk.qy, lk.nx, lk.ny) < 0.f) {
             float tl, tr;
             if (!line_interval(S, k, vmax, tl, tr)) return false;
             const float dx = -lk.ny, dy = lk.nx;
-            const float dd = dx * ox + dy * oy;
+            const float dd = fdot2(dx, ox, dy, oy);
             float t;
             if (dd > 1e-6f) t = tr;
             else if (dd < -1e-6f) t = tl;
-            else t = fminf(fmaxf((pref.x - lk.qx) * dx + (pref.y - lk.qy) * dy, tl), tr);
-            v.x = lk.qx + t * dx;
-            v.y = lk.qy + t * dy;
+            else t = fminf(fmaxf(side_of(pref.x, pref.y, lk.qx, lk.qy, dx, dy), tl), tr);
+            v.x = __fmaf_rn(t, dx, lk.qx);
+            v.y = __fmaf_rn(t, dy, lk.qy);
         }
     }
     return true;
@@ -757,32 +769,32 @@ __device__ __forceinline__ float2 lp_fallback(const Line* L, int n, int n_hard, 
     int solves = 0, solve_lines = 0;
     if (lp2(L, n_hard, vmax, pref, v, solves, solve_lines) < n_hard) {
         n_hard = 0;
-        const float pl2 = pref.x * pref.x + pref.y * pref.y;
-        const float k = pl2 > vmax * vmax ? vmax * rsqrtf(pl2) : 1.f;
+        const float pl2 = fdot2(pref.x, pref.x, pref.y, pref.y);
+        const float k = pl2 > __fmul_rn(vmax, vmax) ? vmax * rsqrtf(pl2) : 1.f;
         v = make_float2(pref.x * k, pref.y * k);
     }
     float dist = -INFINITY;
     for (int i = n_hard; i < n; ++i) {
         const Line li = L[i];
-        const float viol = -((v.x - li.qx) * li.nx + (v.y - li.qy) * li.ny);
+        const float viol = -side_of(v.x, v.y, li.qx, li.qy, li.nx, li.ny);
         if (viol > dist) {
             int m = 0;
             for (int k = 0; k < n_hard; ++k) S[m++] = L[k];
-            const float ci = li.qx * li.nx + li.qy * li.ny;
+            const float ci = fdot2(li.qx, li.nx, li.qy, li.ny);
             for (int j = n_hard; j < i; ++j) {
                 const Line lj = L[j];
                 float nx = lj.nx - li.nx, ny = lj.ny - li.ny;
-                const float nl2 = nx * nx + ny * ny;
+                const float nl2 = fdot2(nx, nx, ny, ny);
                 if (nl2 < 1e-12f) continue;  // same direction: cannot bind at the optimum
                 const float inv = rsqrtf(nl2);
                 nx *= inv;
                 ny *= inv;
-                const float c = ((lj.qx * lj.nx + lj.qy * lj.ny) - ci) * inv;
+                const float c = (fdot2(lj.qx, lj.nx, lj.qy, lj.ny) - ci) * inv;
                 S[m++] = Line{c * nx, c * ny, nx, ny};
             }
             float2 t;
             if (lp_dir(S, m, vmax, li.nx, li.ny, pref, t)) v = t;
-            dist = -((v.x - li.qx) * li.nx + (v.y - li.qy) * li.ny);
+            dist = -side_of(v.x, v.y, li.qx, li.qy, li.nx, li.ny);
         }
     }
     return v;
