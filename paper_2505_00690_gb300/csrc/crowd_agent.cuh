@@ -399,9 +399,11 @@ __device__ __forceinline__ float2 solve_velocity(const AgentParams& a, const Age
         if (s < nb.cnt) {
             const int j = nb.id[s];
             const float4 o = ag.state(j);
-            // all of the avoidance against a vehicle, which does not react
-            const float alpha = (j == robot) ? a.robot_alpha : (ag.vehicle(j) ? 1.f : 0.5f);
-            L[no + s] = agent_line(me.x, me.y, me.z, me.w, pr.x, o.x, o.y, o.z, o.w, ag.radius(j), a.tau, a.dt,
+            // (r, v_max, preferred speed, car flag) of j in one load; all of
+            // the avoidance against a car, which does not react
+            const float4 pj = ag.params(j);
+            const float alpha = (j == robot) ? a.robot_alpha : (pj.w != 0.f ? 1.f : 0.5f);
+            L[no + s] = agent_line(me.x, me.y, me.z, me.w, pr.x, o.x, o.y, o.z, o.w, pj.x, a.tau, a.dt,
                                    alpha, i < j);
         }
     }

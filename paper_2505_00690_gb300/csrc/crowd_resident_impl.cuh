@@ -216,6 +216,7 @@ struct SmemAgents {
     __device__ __forceinline__ float4 state(int j) const { return pv[j]; }
     __device__ __forceinline__ float radius(int j) const { return par[j].x; }
     __device__ __forceinline__ bool vehicle(int j) const { return par[j].w != 0.f; }
+    __device__ __forceinline__ float4 params(int j) const { return par[j]; }
 };
 
 // The segment list of the static segment-grid cell holding position `me`.
@@ -538,6 +539,9 @@ __global__ void __launch_bounds__(kMaxThreads, G >= 4 ? 2 : 1) resident_kernel(R
         double speed_acc = 0.0;
         unsigned long long ca = 0, cs = 0;
         Tally tally;
+        // cars are looked for only in environments that have some (a test per
+        // agent in the others cost the dense crowd a third of its time)
+        const bool env_veh = a.veh.n > 0 && a.veh.start[c.e + 1] > a.veh.start[c.e];
         const AgentParams ap{a.R, a.dt, a.tau, a.tau_o, a.robot_alpha, a.K, a.segs, a.err, a.seg_vd};
         // the queue capacity depends on this environment alone, so that its
         // results do not depend on the batch it runs in
@@ -597,7 +601,7 @@ __global__ void __launch_bounds__(kMaxThreads, G >= 4 ? 2 : 1) resident_kernel(R
                 for (int b = 0; b < c.n; b += blockDim.x) {
                     const int t = b + (a.agent_order ? (threadIdx.x & 31) * warps + (threadIdx.x >> 5) : threadIdx.x);
                     if (t >= c.n) continue;
-                    if (S.par[S.sid[t]].z < 0.f) {  // a car (negative preferred speed)
+                    if (env_veh && S.par[S.sid[t]].z < 0.f) {  // a car (negative preferred speed)
                         vehicle_update<KMAX>(a, S, c, t, speed_acc, tally);
                         S.pend[t] = 0;
                         continue;

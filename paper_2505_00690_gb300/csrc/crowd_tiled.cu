@@ -160,6 +160,7 @@ struct GlobalAgents {
     __device__ __forceinline__ float4 state(int j) const { return pv[j]; }
     __device__ __forceinline__ float radius(int j) const { return __ldg(&par[j]).x; }
     __device__ __forceinline__ bool vehicle(int j) const { return __ldg(&par[j]).w != 0.f; }
+    __device__ __forceinline__ float4 params(int j) const { return __ldg(&par[j]); }
 };
 
 template <int KMAX, class Src>
