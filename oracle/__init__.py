@@ -14,6 +14,10 @@ paper cites for it (van den Berg et al., ISRR 2011):
   min-max-penetration fallback, O7 explicit Euler integration, O8 rollout
   statistics (collision indicator and speed of the paper's metric table,
   Appendix "Evaluation Metrics").
+Around the step: goal queues (advance_goals), episodes that start
+environments over on their own schedules (episode_restarts, restart_rows;
+Sec. 3.3), lane-following cars (``oracle.vehicles``) and the occupancy-map
+front end (``oracle.frontend``).
 """
 from __future__ import annotations
 
@@ -132,6 +136,30 @@ def advance_goals(pos, radius, goal, idx, queue, cyclic, skip=None):
     rows = np.nonzero(move)[0]
     g[rows] = qu[rows, k[rows] % n_goals]
     return g, k
+
+
+def episode_restarts(t, steps):
+    """Episodes (Sec. 3.3: asynchronous scene sampling trains on many
+    environments at once whose episodes differ, so each environment starts
+    over on its own schedule).  Environment e with steps[e] > 0 starts over at
+    the start of step t of the episode clock (the first step after the
+    episodes are set up is t = 0) when t > 0 and t is a multiple of steps[e];
+    steps[e] = 0 never starts over.  Returns the [E] bool mask."""
+    st = np.asarray(steps, np.int64).reshape(-1)
+    t = int(t)
+    return (st > 0) & (t > 0) & (t % np.maximum(st, 1) == 0)
+
+
+def restart_rows(t, steps, owner, current, snapshot):
+    """The rows of `current` whose environment owner[row] starts over at step
+    t (episode_restarts) take the rows of `snapshot`; the others are kept.
+    Applied at the start of the step, before anything else of it (goal queues,
+    cars, the robot command), so the state read after the step that ends an
+    episode is that episode's last state.  Returns a new array."""
+    out = np.array(current, copy=True)
+    sel = episode_restarts(t, steps)[np.asarray(owner, np.int64).reshape(-1)]
+    out[sel] = np.asarray(snapshot)[sel]
+    return out
 
 
 def rank_key(pi, pj):
