@@ -196,6 +196,25 @@ crowd_status crowd_set_vehicles(crowd_t h, int32_t n_lanes, const int32_t* lane_
  * when `write` != 0 (s in [0, lane length), v >= 0), else read.  Waits. */
 crowd_status crowd_vehicle_state(crowd_t h, int32_t write, float* s, float* v);
 
+/* Episodes: environments start over inside multi-step calls, each on its own
+ * schedule (the paper trains on many environments at once whose episodes
+ * differ, Sec. 3.3).  The episode clock reads t = 0 at the next step after
+ * this call.  Environment e with steps[e] > 0 starts over at the start of
+ * every step t > 0 that is a multiple of steps[e], before anything else of
+ * that step: its agent rows become those of init_state ([N][4], host or
+ * device per ptr_kind; NULL: the state at this call), and its goals,
+ * goal-queue counters and car arc states become those at this call.  The
+ * state read after the step that ends an episode is the episode's last
+ * state.  Statistics run on across starts: collisions count every
+ * post-integration state (episode ends included, restored states not),
+ * first-reach steps keep their first value.
+ *   steps [n_envs] host, >= 0 (0: never); NULL or all 0 removes the episodes,
+ *   as do crowd_set_goals, crowd_set_goal_queue and crowd_set_vehicles.
+ * crowd_reset_stats leaves the episode clock running.  The serving loop and
+ * crowd_step_noalloc have no episodes.  CROWD_EINVAL: steps[e] < 0, NaN/Inf
+ * in a host init_state.  Copies; waits for the stream. */
+crowd_status crowd_set_episodes(crowd_t h, const int32_t* steps, const float* init_state, int32_t ptr_kind);
+
 /* Full state [N][4] (px, py, vx, vy): resume from a checkpoint, or teacher
  * forcing from another simulator's state. */
 crowd_status crowd_set_state(crowd_t h, const float* state, int32_t ptr_kind);

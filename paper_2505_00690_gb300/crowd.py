@@ -30,7 +30,7 @@ EXPORTED = ["crowd_create", "crowd_set_goals", "crowd_set_state", "crowd_step", 
             "crowd_read_neighbors", "crowd_read_stats", "crowd_read_work", "crowd_reset_stats", "crowd_synchronize",
             "crowd_destroy", "crowd_num_agents", "crowd_num_envs", "crowd_last_error", "crowd_abi_version",
             "crowd_get_tuning", "crowd_set_tuning", "crowd_autotune", "crowd_set_goal_queue",
-            "crowd_read_goal_index", "crowd_set_vehicles", "crowd_vehicle_state"]
+            "crowd_read_goal_index", "crowd_set_vehicles", "crowd_vehicle_state", "crowd_set_episodes"]
 
 
 class CrowdError(RuntimeError):
@@ -76,6 +76,7 @@ def load(path: str = LIB_PATH):
     L.crowd_set_goals.argtypes = [vp, vp, i32]
     L.crowd_set_goal_queue.argtypes = [vp, i32, vp, i32, i32]
     L.crowd_read_goal_index.argtypes = [vp, vp]
+    L.crowd_set_episodes.argtypes = [vp, vp, vp, i32]
     L.crowd_set_vehicles.argtypes = [vp, i32, vp, vp, i32, vp, vp, vp, vp, vp, C.c_float, C.c_float]
     L.crowd_vehicle_state.argtypes = [vp, i32, vp, vp]
     L.crowd_set_state.argtypes = [vp, vp, i32]
@@ -273,6 +274,16 @@ class Crowd:
         q = np.ascontiguousarray(queue, np.float32)
         assert q.ndim == 3 and q.shape[0] == self.N and q.shape[2] == 2
         _check(load().crowd_set_goal_queue(self.h, int(q.shape[1]), q.ctypes.data, int(bool(cyclic)), CROWD_HOST))
+
+    def set_episodes(self, steps, init_state=None):
+        """Per-environment episode lengths [E] (0: never; None: remove) and the
+        rows they start from (None: the current state); see crowd_set_episodes."""
+        st = None if steps is None else np.ascontiguousarray(steps, np.int32)
+        assert st is None or st.shape == (self.E,)
+        init = None if init_state is None else np.ascontiguousarray(init_state, np.float32)
+        assert init is None or init.shape == (self.N, 4)
+        _check(load().crowd_set_episodes(self.h, None if st is None else st.ctypes.data,
+                                         None if init is None else init.ctypes.data, CROWD_HOST))
 
     def set_vehicles(self, veh):
         """Lane-following cars (scenes.Vehicles; see crowd_set_vehicles)."""

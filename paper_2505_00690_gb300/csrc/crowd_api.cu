@@ -84,6 +84,13 @@ struct crowd_ctx {
     int* goal_idx = nullptr;       // [N]
     int goal_q = 0, goal_cyclic = 0;
     size_t goal_queue_cap = 0;     // entries allocated in goal_queue
+    int* ep_steps = nullptr;       // [E] episode lengths (crowd_set_episodes); null: no episodes
+    float4* ep_state = nullptr;    // [N] agent rows at the start of an episode
+    float2* ep_goal = nullptr;     // [N] goals at the start of an episode
+    int* ep_gidx = nullptr;        // [N] goal-queue counters at the start (with a queue)
+    float* ep_veh = nullptr;       // [2V] car arcs at the start (with cars): s | v
+    int64_t ep_origin = 0;         // step_index at which the episode clock reads 0
+    std::vector<int> h_ep_steps;   // host copy of ep_steps (empty: no episodes)
     // lane-following vehicles (crowd_set_vehicles)
     int n_veh = 0;
     int* veh_start = nullptr;      // [E + 1]
@@ -110,6 +117,7 @@ struct crowd_ctx {
 
     // resident path: environments that fit one CTA (the first n_res of `order`)
     int n_res = 0;
+    std::vector<int> h_res_envs;  // host copy of the first n_res entries of `order`
     int res_max_agents = 0;
     int res_max_work = 0;  // largest count of solved (non-robot) agents of a resident environment
     int block = 0, grid = 0;  // resident launch shape for `tune`
@@ -137,7 +145,10 @@ struct crowd_ctx {
         int n_steps = 0;
         float dt = 0.f;
         const void* rv = nullptr;
-        bool operator==(const GraphKey& o) const { return n_steps == o.n_steps && dt == o.dt && rv == o.rv; }
+        std::vector<int> stats_before;  // steps preceded by a statistics pass (episode starts)
+        bool operator==(const GraphKey& o) const {
+            return n_steps == o.n_steps && dt == o.dt && rv == o.rv && stats_before == o.stats_before;
+        }
     } gkey;
 
     ~crowd_ctx() {
@@ -145,7 +156,7 @@ struct crowd_ctx {
         if (cap_stream) cudaStreamDestroy(cap_stream);
         void* ptrs[] = {env_start, seg_start, robot_index, order, queue, err, state, par, goal, goal_queue, goal_idx,
                         veh_start, veh_agent, veh_lane, veh_s, veh_v, veh_par_a, veh_par_b, lane_pts, lane_start,
-                        lane_cum, veh_pref,
+                        lane_cum, veh_pref, ep_steps, ep_state, ep_goal, ep_gidx, ep_veh,
                         segs, robot_vel, nbr, reach, stats, work, tenvs, state_b, sorted_pv, key, rank,
                         count, start, sorted_id, seg_cell_start, seg_cell_ids, seg_grid, d_step};
         for (void* q : ptrs)
@@ -260,6 +271,58 @@ void drop_graph(crowd_t h) {
     }
 }
 
+// Episodes snapshot goals, goal-queue counters and cars: setting any of them
+// again removes the episodes.
+void drop_episodes(crowd_t h) {
+    if (h->h_ep_steps.empty()) return;
+    void** ps[] = {(void**)&h->ep_steps, (void**)&h->ep_state, (void**)&h->ep_goal, (void**)&h->ep_gidx,
+                   (void**)&h->ep_veh};
+    cudaStreamSynchronize(h->stream);
+    for (void** q : ps)
+        if (*q) {
+            cudaFree(*q);
+            *q = nullptr;
+        }
+    h->h_ep_steps.clear();
+    drop_graph(h);
+}
+
+EpisodeArgs episode_args(crowd_t h) {
+    EpisodeArgs ep{};
+    if (h->h_ep_steps.empty()) return ep;
+    ep.steps = h->ep_steps;
+    ep.state = h->ep_state;
+    ep.goal = h->ep_goal;
+    ep.gidx = h->ep_gidx;
+    ep.veh_s = h->ep_veh;
+    ep.veh_v = h->ep_veh ? h->ep_veh + h->n_veh : nullptr;
+    ep.origin = h->ep_origin;
+    return ep;
+}
+
+// Episodes of the resident environments: environment order[blockIdx.y]
+// takes its episode-start rows, goals, goal-queue counters and car arcs when
+// its episode starts at global step `step`.
+__global__ void restart_resident_envs(EpisodeArgs ep, const int* order, const int* env_start, VehicleArgs veh,
+                                      float4* state, float2* goal, int* gidx, long long step) {
+    const int e = order[blockIdx.y];
+    if (!episode_restart(ep.steps[e], step, ep.origin)) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int g = env_start[e] + i;
+    if (g < env_start[e + 1]) {
+        state[g] = ep.state[g];
+        goal[g] = ep.goal[g];
+        if (ep.gidx) gidx[g] = ep.gidx[g];
+    }
+    if (ep.veh_s) {
+        const int vi = veh.start[e] + i;
+        if (vi < veh.start[e + 1]) {
+            veh.s[vi] = ep.veh_s[vi];
+            veh.v[vi] = ep.veh_v[vi];
+        }
+    }
+}
+
 crowd_status check_handle(crowd_t h) {
     if (!h) return fail(CROWD_EINVAL, "null handle");
     if (h->broken) return fail(CROWD_ESTATE, "handle is unusable after an earlier CUDA failure");
@@ -359,8 +422,8 @@ void apply_tuning(crowd_t h, const Tuning& t) {
 }
 
 // Enqueue n steps of the resident environments on `s`.
-crowd_status resident_steps(crowd_t h, float dt, const float2* rv, int n_steps, bool stats, float tau_o,
-                            cudaStream_t s) {
+crowd_status resident_launch(crowd_t h, float dt, const float2* rv, int n_steps, int64_t step_base, bool stats,
+                             float tau_o, cudaStream_t s) {
     ResidentArgs a{};
     a.n_work = h->n_res;
     a.order = h->order;
@@ -391,7 +454,7 @@ crowd_status resident_steps(crowd_t h, float dt, const float2* rv, int n_steps, 
     a.nbr_out = h->nbr;
     a.stats = stats ? h->stats : nullptr;
     a.reach = stats ? h->reach : nullptr;
-    a.step_base = h->step_index;
+    a.step_base = step_base;
     a.work = h->work;
     a.err = h->err;
     a.max_agents = h->res_max_agents;
@@ -408,6 +471,56 @@ crowd_status resident_steps(crowd_t h, float dt, const float2* rv, int n_steps, 
     return CROWD_OK;
 }
 
+// Steps k in [0, n_steps) of a call at whose start a resident environment
+// starts over (episodes).
+std::vector<int> resident_restart_steps(crowd_t h, int n_steps) {
+    std::vector<char> mark(n_steps, 0);
+    if (!h->h_ep_steps.empty())
+        for (int e : h->h_res_envs) {
+            const long long L = h->h_ep_steps[e];
+            if (L <= 0) continue;
+            const long long t0 = h->step_index - h->ep_origin;  // clock at k = 0
+            long long t = t0 <= 0 ? L : ((t0 + L - 1) / L) * L;
+            for (; t - t0 < n_steps; t += L) mark[t - t0] = 1;
+        }
+    std::vector<int> out;
+    for (int k = 0; k < n_steps; ++k)
+        if (mark[k]) out.push_back(k);
+    return out;
+}
+
+// n steps of the resident environments.  With episodes the call is split at
+// the steps where a resident environment starts over, and the starts run
+// between the launches, so the step kernel carries no episode code: each
+// launch counts its final state in the statistics and the next one does not
+// count its first, so an episode's last state is counted and the restored
+// start not.
+crowd_status resident_steps(crowd_t h, float dt, const float2* rv, int n_steps, bool stats, float tau_o,
+                            cudaStream_t s) {
+    const std::vector<int> starts = resident_restart_steps(h, n_steps);
+    if (starts.empty()) return resident_launch(h, dt, rv, n_steps, h->step_index, stats, tau_o, s);
+    const EpisodeArgs ep = episode_args(h);
+    const VehicleArgs veh{h->n_veh, h->veh_start, h->veh_agent, h->veh_lane, h->veh_s, h->veh_v, h->veh_par_a,
+                          h->veh_par_b, h->lane_pts, h->lane_start, h->lane_cum, h->veh_half_width, h->veh_lookahead};
+    const int span = std::max(h->res_max_agents, CROWD_MAX_VEHICLES_PER_ENV);
+    int k = 0;
+    size_t q = 0;
+    while (k < n_steps) {
+        if (q < starts.size() && starts[q] == k) {
+            ++q;
+            restart_resident_envs<<<dim3((span + 255) / 256, h->n_res), 256, 0, s>>>(
+                ep, h->order, h->env_start, veh, h->state, h->goal, h->goal_idx, h->step_index + k);
+            CUDA_TRY(cudaGetLastError(), "episode start");
+        }
+        const int next = q < starts.size() ? starts[q] : n_steps;
+        crowd_status st = resident_launch(h, dt, rv ? rv + (size_t)k * h->E : nullptr, next - k, h->step_index + k,
+                                          stats, tau_o, s);
+        if (st) return st;
+        k = next;
+    }
+    return CROWD_OK;
+}
+
 // Arguments of step s (0-based) of an n-step tiled sequence.
 TiledStepArgs tiled_args(crowd_t h, float dt, const float2* rv, int s, int n_steps, bool stats, float tau_o,
                          int mode) {
@@ -420,6 +533,7 @@ TiledStepArgs tiled_args(crowd_t h, float dt, const float2* rv, int s, int n_ste
     a.par = h->par;
     a.goal = h->goal;
     a.goals = GoalQueue{h->goal_queue, h->goal_idx, h->goal_q, h->goal_cyclic};
+    a.ep = episode_args(h);
     a.seg_vd = (h->p.flags & CROWD_FLAG_VELOCITY_SEGMENTS) ? 1 : 0;
     a.segs = h->segs;
     a.seg_cell_start = h->seg_cell_start;
@@ -447,13 +561,39 @@ TiledStepArgs tiled_args(crowd_t h, float dt, const float2* rv, int s, int n_ste
     return a;
 }
 
+// Steps k (0 < k < n_steps) of an n-step tiled call at whose start a tiled
+// environment starts over, when statistics are on.
+std::vector<int> tiled_stats_before(crowd_t h, int n_steps, bool stats) {
+    std::vector<int> out;
+    if (!stats || h->h_ep_steps.empty()) return out;
+    for (int k = 1; k < n_steps; ++k)
+        for (const TiledEnv& te : h->h_tenvs)
+            if (te.n && episode_restart(h->h_ep_steps[te.e], h->step_index + k, h->ep_origin)) {
+                out.push_back(k);
+                break;
+            }
+    return out;
+}
+
 // Enqueue an n-step tiled sequence on `s`: the steps alternate between the
 // two state buffers; an odd count ends with the tiled environments copied
 // back; with statistics a last pass counts the collisions of the final state.
 cudaError_t enqueue_tiled(crowd_t h, float dt, const float2* rv, int n_steps, bool stats, float tau_o,
                           cudaStream_t s) {
+    const std::vector<int> before = tiled_stats_before(h, n_steps, stats);
+    size_t nb = 0;
     for (int k = 0; k < n_steps; ++k) {
-        const int mode = (stats && k > 0) ? kTiledStepCount : kTiledStep;
+        const bool apart = nb < before.size() && before[nb] == k;
+        if (apart) {
+            // an environment starts over at step k: the statistics of every
+            // environment's state at the start of k are counted first, so
+            // that an episode's last state is counted and its restart not
+            ++nb;
+            cudaError_t e = launch_tiled_step(tiled_args(h, dt, nullptr, k, n_steps, stats, tau_o, kTiledStatsOnly),
+                                              h->tiled_max_agents, h->tiled_max_tiles, s);
+            if (e != cudaSuccess) return e;
+        }
+        const int mode = (stats && k > 0 && !apart) ? kTiledStepCount : kTiledStep;
         cudaError_t e = launch_tiled_step(tiled_args(h, dt, rv, k, n_steps, stats, tau_o, mode), h->tiled_max_agents,
                                           h->tiled_max_tiles, s);
         if (e != cudaSuccess) return e;
@@ -489,6 +629,7 @@ crowd_status tiled_steps(crowd_t h, float dt, const float2* rv, int n_steps, boo
     key.n_steps = n_steps;
     key.dt = dt;
     key.rv = rv;
+    key.stats_before = tiled_stats_before(h, n_steps, stats);
     if (!h->graph || !(key == h->gkey)) {
         if (h->graph) {
             cudaGraphExecDestroy(h->graph);
@@ -619,6 +760,7 @@ crowd_status crowd_create(int32_t n_envs, const int32_t* agents_per_env, const f
         h->res_max_work = std::max(h->res_max_work, (int)agents_per_env[e] - (has_robot ? 1 : 0));
     }
     h->n_res = (int)order.size();
+    h->h_res_envs = order;
     h->n_tiled = (int)tiled.size();
     std::vector<int> seg_cell_start, seg_cell_ids;
     int total_cells = 0;
@@ -764,6 +906,7 @@ crowd_status crowd_set_goals(crowd_t h, const float* goals, int32_t ptr_kind) {
     if (h->N == 0) return CROWD_OK;
     if (!goals) return fail(CROWD_EINVAL, "goals is null");
     if (ptr_kind == CROWD_HOST && !finite_all(goals, (size_t)h->N * 2)) return fail(CROWD_EINVAL, "goals hold NaN/Inf");
+    drop_episodes(h);
     if (h->goal_q) {
         h->goal_q = 0;  // fixed goals replace a goal queue
         drop_graph(h);
@@ -781,6 +924,7 @@ crowd_status crowd_set_goal_queue(crowd_t h, int32_t n_goals, const float* goals
     const size_t count = (size_t)h->N * n_goals;
     if (ptr_kind == CROWD_HOST && !finite_all(goals, count * 2)) return fail(CROWD_EINVAL, "goals hold NaN/Inf");
     CUDA_TRY(cudaStreamSynchronize(h->stream), "synchronize");
+    drop_episodes(h);
     if (h->goal_queue && h->goal_queue_cap < count) {
         cudaFree(h->goal_queue);
         h->goal_queue = nullptr;
@@ -881,6 +1025,7 @@ crowd_status crowd_set_vehicles(crowd_t h, int32_t n_lanes, const int32_t* lane_
         cumf.assign(cum.begin(), cum.end());
     }
     CUDA_TRY(cudaStreamSynchronize(h->stream), "synchronize");
+    drop_episodes(h);
     // unmark the old cars, release the old arrays
     if (h->n_veh > 0) {
         mark_vehicles<<<(h->n_veh + 255) / 256, 256, 0, h->stream>>>(h->par, h->veh_agent, h->n_veh, 0, h->veh_pref);
@@ -977,6 +1122,58 @@ crowd_status crowd_read_goal_index(crowd_t h, int32_t* out) {
     }
     CUDA_TRY(cudaMemcpyAsync(out, h->goal_idx, sizeof(int) * h->N, cudaMemcpyDeviceToHost, h->stream), "copy goal counters");
     CUDA_TRY(cudaStreamSynchronize(h->stream), "synchronize");
+    return CROWD_OK;
+}
+
+crowd_status crowd_set_episodes(crowd_t h, const int32_t* steps, const float* init_state, int32_t ptr_kind) {
+    crowd_status st = check_handle(h);
+    if (st) return st;
+    if (ptr_kind != CROWD_HOST && ptr_kind != CROWD_DEVICE) return fail(CROWD_EINVAL, "ptr_kind must be 0 or 1");
+    bool any = false;
+    if (steps)
+        for (int e = 0; e < h->E; ++e) {
+            if (steps[e] < 0) return fail(CROWD_EINVAL, "steps[%d] must be >= 0", e);
+            any |= steps[e] > 0;
+        }
+    if (init_state && ptr_kind == CROWD_HOST && !finite_all(init_state, (size_t)h->N * 4))
+        return fail(CROWD_EINVAL, "init_state holds NaN/Inf");
+    CUDA_TRY(cudaStreamSynchronize(h->stream), "synchronize");
+    drop_episodes(h);
+    if (!any || h->N == 0) return CROWD_OK;
+    // the episodes exist once every snapshot below is in place
+    auto undo = [&](crowd_status s) {
+        h->h_ep_steps.assign(1, 0);
+        drop_episodes(h);
+        return s;
+    };
+    cudaError_t e = dev_alloc(&h->ep_steps, (size_t)h->E);
+    if (e == cudaSuccess) e = dev_alloc(&h->ep_state, (size_t)h->N);
+    if (e == cudaSuccess) e = dev_alloc(&h->ep_goal, (size_t)h->N);
+    if (e == cudaSuccess && h->goal_q) e = dev_alloc(&h->ep_gidx, (size_t)h->N);
+    if (e == cudaSuccess && h->n_veh) e = dev_alloc(&h->ep_veh, 2 * (size_t)h->n_veh);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h->ep_steps, steps, sizeof(int) * h->E, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess && !init_state)
+        e = cudaMemcpyAsync(h->ep_state, h->state, sizeof(float4) * h->N, cudaMemcpyDeviceToDevice, h->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h->ep_goal, h->goal, sizeof(float2) * h->N, cudaMemcpyDeviceToDevice, h->stream);
+    if (e == cudaSuccess && h->goal_q)
+        e = cudaMemcpyAsync(h->ep_gidx, h->goal_idx, sizeof(int) * h->N, cudaMemcpyDeviceToDevice, h->stream);
+    if (e == cudaSuccess && h->n_veh)
+        e = cudaMemcpyAsync(h->ep_veh, h->veh_s, sizeof(float) * h->n_veh, cudaMemcpyDeviceToDevice, h->stream);
+    if (e == cudaSuccess && h->n_veh)
+        e = cudaMemcpyAsync(h->ep_veh + h->n_veh, h->veh_v, sizeof(float) * h->n_veh, cudaMemcpyDeviceToDevice,
+                            h->stream);
+    if (e != cudaSuccess) return undo(cuda_fail(e, "set episodes"));
+    if (init_state) {
+        st = copy_in(h, h->ep_state, init_state, sizeof(float4) * h->N, ptr_kind, "copy episode state");
+        if (st) return undo(st);
+    }
+    e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return undo(cuda_fail(e, "set episodes"));
+    h->h_ep_steps.assign(steps, steps + h->E);
+    h->ep_origin = h->step_index;
+    drop_graph(h);
     return CROWD_OK;
 }
 
@@ -1237,6 +1434,7 @@ crowd_status crowd_reset_stats(crowd_t h) {
     if (st) return st;
     if (h->N) CUDA_TRY(cudaMemsetAsync(h->reach, 0xff, sizeof(int) * h->N, h->stream), "reset reach");
     if (h->E) CUDA_TRY(cudaMemsetAsync(h->stats, 0, sizeof(EnvStats) * h->E, h->stream), "reset stats");
+    h->ep_origin -= h->step_index;  // the episode clock runs on
     h->step_index = 0;
     return CROWD_OK;
 }

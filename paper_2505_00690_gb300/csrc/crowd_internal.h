@@ -31,6 +31,25 @@ struct VehicleArgs {
     float half_width, lookahead;
 };
 
+// Episodes of a handle (see crowd_set_episodes): environment e starts over
+// at the start of step t of the episode clock when steps[e] > 0, t > 0 and
+// t % steps[e] == 0, restoring its rows from the snapshot taken when the
+// episodes were set.
+struct EpisodeArgs {
+    const int* steps;     // [E] episode length in steps (0: never); null: no episodes
+    const float4* state;  // [N] agent rows at the start of an episode
+    const float2* goal;   // [N] goals at the start of an episode
+    const int* gidx;      // [N] goal-queue counters at the start (null: no queue)
+    const float* veh_s;   // [V] car arc positions at the start (null: no cars)
+    const float* veh_v;   // [V] car speeds at the start
+    long long origin;     // global step index of the episode clock's t = 0
+};
+
+__host__ __device__ inline bool episode_restart(int steps, long long global_step, long long origin) {
+    const long long t = global_step - origin;
+    return steps > 0 && t > 0 && t % steps == 0;
+}
+
 // Device error word bits.
 enum : int {
     kErrObstacleOverflow = 1,  // an agent had more segments in reach than the line buffer holds
@@ -156,6 +175,7 @@ struct TiledStepArgs {
     const float4* par;
     float2* goal;             // [N] current goals (advanced in tiled_count with a goal queue)
     GoalQueue goals;
+    EpisodeArgs ep;
     const float4* segs;
     const int* seg_cell_start;  // [cells + 1 per env] per-cell segment lists
     const int* seg_cell_ids;

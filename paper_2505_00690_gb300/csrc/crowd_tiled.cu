@@ -50,13 +50,21 @@ __global__ void __launch_bounds__(kCountThreads) tiled_count(TiledStepArgs a) {
     if (i >= te.n) return;
     const int g = te.base + i;
     float4 p = a.state_in[g];
+    if (a.mode != kTiledStatsOnly && a.ep.steps && episode_restart(a.ep.steps[te.e], *a.step_index, a.ep.origin)) {
+        // episodes: the environment starts over (the host counted the
+        // statistics of the episode's last state before this step)
+        p = a.ep.state[g];
+        a.state_in[g] = p;
+        a.goal[g] = a.ep.goal[g];
+        if (a.ep.gidx) a.goals.idx[g] = a.ep.gidx[g];
+    }
     if (i == te.robot && a.robot_vel) {
         const float2 cmd = __ldg(&a.robot_vel[te.e]);
         p.z = cmd.x;
         p.w = cmd.y;
         a.state_in[g] = p;
     }
-    if (a.goals.q > 0 && i != te.robot) {
+    if (a.goals.q > 0 && i != te.robot && a.mode != kTiledStatsOnly) {
         const float2 cur = a.goal[g];
         const float2 nx = advance_goal(a.goals, g, p, __ldg(&a.par[g]).x, cur);
         if (nx.x != cur.x || nx.y != cur.y) a.goal[g] = nx;
@@ -158,8 +166,6 @@ struct GlobalAgents {
     const float4* pv;
     const float4* par;
     __device__ __forceinline__ float4 state(int j) const { return pv[j]; }
-    __device__ __forceinline__ float radius(int j) const { return __ldg(&par[j]).x; }
-    __device__ __forceinline__ bool vehicle(int j) const { return __ldg(&par[j]).w != 0.f; }
     __device__ __forceinline__ float4 params(int j) const { return __ldg(&par[j]); }
 };
 
