@@ -400,6 +400,7 @@ void build_tiled_env(int e, int base, int n, int seg0, int ns, int robot, const 
     const double cc = 1.0 / (double)te.inv_c;
     te.W = std::min(kTiledGridMax, (int)((x1 - x0) / cc) + 1);
     te.H = std::min(kTiledGridMax, (int)((y1 - y0) / cc) + 1);
+    choose_tile(n, te.W, te.H, te.tx, te.ty);
 
     build_seg_lists(segs, seg0, ns, x0, y0, cc, te.W, te.H,
                     seg_reach(base, n, radii, vmax, p.time_horizon, p.time_horizon_obst), co, seg_cell_start,
@@ -771,7 +772,7 @@ crowd_status crowd_create(int32_t n_envs, const int32_t* agents_per_env, const f
                         seg_cell_ids);
         total_cells += te.W * te.H + 1;
         h->tiled_max_agents = std::max(h->tiled_max_agents, te.n);
-        h->tiled_max_tiles = std::max(h->tiled_max_tiles, ((te.W + kTile - 1) / kTile) * ((te.H + kTile - 1) / kTile));
+        h->tiled_max_tiles = std::max(h->tiled_max_tiles, ((te.W + te.tx - 1) / te.tx) * ((te.H + te.ty - 1) / te.ty));
         h->h_tenvs.push_back(te);
     }
     std::vector<SegGrid> seg_grids(std::max(n_envs, 1));

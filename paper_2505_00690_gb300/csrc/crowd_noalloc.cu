@@ -221,6 +221,7 @@ extern "C" crowd_status crowd_step_noalloc(int32_t n_agents, const float* state_
     const double cc = 1.0 / (double)te.inv_c;
     te.W = std::min(kNaGridSide, (int)((box[2] - box[0]) / cc) + 1);
     te.H = std::min(kNaGridSide, (int)((box[3] - box[1]) / cc) + 1);
+    choose_tile(n_agents, te.W, te.H, te.tx, te.ty);
     const int C = te.W * te.H;
     if (C > kNaCells) return api_fail(CROWD_EINVAL, "grid of %d cells exceeds %d", C, kNaCells);
 
@@ -285,7 +286,7 @@ extern "C" crowd_status crowd_step_noalloc(int32_t n_agents, const float* state_
     a.mode = kTiledStep;
     a.step_index = &misc->step;
     a.err = &misc->err;
-    const int max_tiles = ((te.W + kTile - 1) / kTile) * ((te.H + kTile - 1) / kTile);
+    const int max_tiles = ((te.W + te.tx - 1) / te.tx) * ((te.H + te.ty - 1) / te.ty);
     NA_TRY(launch_tiled_step(a, n_agents, max_tiles, s), "allocation-free step");
 #undef NA_TRY
     return CROWD_OK;

@@ -9,7 +9,8 @@
 //   tiled_scan     one CTA per environment turns the counts into cell starts
 //                  (block scan) and clears the counts for the next step;
 //   tiled_scatter  writes the state in cell order;
-//   tiled_update   one CTA per (environment, tile of kTile x kTile cells):
+//   tiled_update   one CTA per (environment, tile of tx x ty cells, sized on
+//                  the host so that a tile's agents fill one round of threads):
 //                  stages the tile's halo cells (already contiguous in cell
 //                  order) into shared memory, then each thread takes the
 //                  tile's agents: K nearest from the staged halo, segment
@@ -241,17 +242,17 @@ __device__ __forceinline__ void tile_agent(const TiledStepArgs& a, const AgentPa
 template <int KMAX>
 __global__ void __launch_bounds__(kUpdateThreads) tiled_update(TiledStepArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ int s_row_slot[kTile + 2], s_row_off[kTile + 2], s_row_cnt[kTile + 2];
-    __shared__ int s_tile_row_slot[kTile], s_tile_row_cnt[kTile];
+    __shared__ int s_row_slot[kTileMax + 2], s_row_off[kTileMax + 2], s_row_cnt[kTileMax + 2];
+    __shared__ int s_tile_row_slot[kTileMax], s_tile_row_cnt[kTileMax];
     __shared__ int s_total, s_tile_total;
     __shared__ unsigned long long s_ca, s_cs;
     __shared__ double s_speed;
     const TiledEnv te = a.envs[blockIdx.y];
     const int tile = blockIdx.x;
-    const int tiles_x = (te.W + kTile - 1) / kTile, tiles_y = (te.H + kTile - 1) / kTile;
+    const int tiles_x = (te.W + te.tx - 1) / te.tx, tiles_y = (te.H + te.ty - 1) / te.ty;
     if (tile >= tiles_x * tiles_y) return;
-    const int tx0 = (tile % tiles_x) * kTile, ty0 = (tile / tiles_x) * kTile;
-    const int tx1 = min(tx0 + kTile, te.W) - 1, ty1 = min(ty0 + kTile, te.H) - 1;
+    const int tx0 = (tile % tiles_x) * te.tx, ty0 = (tile / tiles_x) * te.ty;
+    const int tx1 = min(tx0 + te.tx, te.W) - 1, ty1 = min(ty0 + te.ty, te.H) - 1;
     const int hx0 = max(tx0 - 1, 0), hx1 = min(tx1 + 1, te.W - 1);
     const int hy0 = max(ty0 - 1, 0), hy1 = min(ty1 + 1, te.H - 1);
     const int* start = a.start + te.co;
