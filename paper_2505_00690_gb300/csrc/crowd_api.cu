@@ -356,12 +356,13 @@ crowd_status read_err_word(crowd_t h) {
 
 
 // Static grid of a tiled environment: the bounding box of its agents' start
-// positions and its segments, padded by R, with cells of at least R (times a
-// margin for FP32 rounding of cell coordinates) and at most kTiledGridMax a
-// side; and for every cell the ascending list of the environment's segments
-// that can come within r + tau_obst v_max of a point of the cell.  Agents that
-// leave the box are clamped into its border cells, which keeps both the 3x3
-// neighbour search and the segment lists exact.
+// positions and its segments, padded by R, with cells of at least R / span
+// (times a margin for FP32 rounding of cell coordinates) and at most
+// kTiledGridMax a side; and for every cell the ascending list of the
+// environment's segments that can come within r + tau_obst v_max of a point
+// of the cell.  Agents that leave the box are clamped into its border cells,
+// which keeps both the (2 span + 1)^2-cell neighbour search and the segment
+// lists exact.
 void build_tiled_env(int e, int base, int n, int seg0, int ns, int robot, const float* pos, const float* radii,
                      const float* vmax, const float* segs, const crowd_params& p, int co, TiledEnv& te,
                      std::vector<int>& seg_cell_start, std::vector<int>& seg_cell_ids) {
@@ -386,7 +387,13 @@ void build_tiled_env(int e, int base, int n, int seg0, int ns, int robot, const 
     x1 += R;
     y1 += R;
     const double ext = std::max(x1 - x0, y1 - y0);
-    const float c = (float)std::max(R * 1.0001, ext / (kTiledGridMax - 1));
+    // cells of R / 2 (5 x 5 cells searched, about 30 % fewer candidates than
+    // 3 x 3 cells of R) when a cell still holds every colliding pair, so
+    // that the +-1-cell collision count stays exact
+    double rmax = 0.0;
+    for (int i = 0; i < n; ++i) rmax = std::max(rmax, (double)radii[base + i]);
+    te.span = R * 0.5 >= 2.0 * rmax ? kTiledSpanMax : 1;
+    const float c = (float)std::max(R * 1.0001 / te.span, ext / (kTiledGridMax - 1));
     te.e = e;
     te.base = base;
     te.n = n;

@@ -157,10 +157,13 @@ struct TiledEnv {
     int W, H;       // grid cells
     float x0, y0, inv_c;
     int tx, ty;     // cells per tile of the update kernel (choose_tile)
+    int span;       // cells searched on each side of an agent's cell (cells >= R / span)
 };
 
 // Largest side, in cells, of a tile of the tiled update kernel.
 constexpr int kTileMax = 8;
+// Largest neighbour-search span of a tiled environment (cells of R / 2).
+constexpr int kTiledSpanMax = 2;
 // Agents a tile of the update kernel (256 threads) should hold on average.
 constexpr double kTileFill = 230.0;
 

@@ -222,6 +222,7 @@ extern "C" crowd_status crowd_step_noalloc(int32_t n_agents, const float* state_
     te.W = std::min(kNaGridSide, (int)((box[2] - box[0]) / cc) + 1);
     te.H = std::min(kNaGridSide, (int)((box[3] - box[1]) / cc) + 1);
     choose_tile(n_agents, te.W, te.H, te.tx, te.ty);
+    te.span = 1;
     const int C = te.W * te.H;
     if (C > kNaCells) return api_fail(CROWD_EINVAL, "grid of %d cells exceeds %d", C, kNaCells);
 

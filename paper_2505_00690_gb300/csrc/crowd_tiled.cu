@@ -5,7 +5,8 @@
 // agents than one SM's shared memory.  For such environments one step is
 // four kernels over global memory:
 //   tiled_count    robot command, cell key (static per-environment grid with
-//                  cell size >= R) and rank inside the cell (atomic count);
+//                  cells >= R / span, span 1 or 2) and rank inside the cell
+//                  (atomic count);
 //   tiled_scan     one CTA per environment turns the counts into cell starts
 //                  (block scan) and clears the counts for the next step;
 //   tiled_scatter  writes the state in cell order;
@@ -18,7 +19,7 @@
 //                  agent half-planes, LP, integration into the other buffer.
 // Multi-step calls replay these launches from a CUDA graph (captured by the
 // host side).  Agents outside the grid are clamped into the border cells,
-// which keeps the 3x3-cell search exact (clamping onto a box is
+// which keeps the (2 span + 1)^2-cell search exact (clamping onto a box is
 // non-expansive).
 #include <cuda_runtime.h>
 #include <math.h>
@@ -206,7 +207,7 @@ __device__ __forceinline__ void tile_agent(const TiledStepArgs& a, const AgentPa
     }
 
     NbList<KMAX> nb;
-    select_neighbors<KMAX>(src, cx, cy, te.W, te.H, i, me, ap.R, ap.K, nb, w);
+    select_neighbors<KMAX>(src, cx, cy, te.W, te.H, i, me, ap.R, ap.K, nb, w, te.span);
     if (a.nbr_out) {
         int* out = a.nbr_out + (size_t)g * ap.K;
 #pragma unroll
@@ -242,7 +243,8 @@ __device__ __forceinline__ void tile_agent(const TiledStepArgs& a, const AgentPa
 template <int KMAX>
 __global__ void __launch_bounds__(kUpdateThreads) tiled_update(TiledStepArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ int s_row_slot[kTileMax + 2], s_row_off[kTileMax + 2], s_row_cnt[kTileMax + 2];
+    __shared__ int s_row_slot[kTileMax + 2 * kTiledSpanMax], s_row_off[kTileMax + 2 * kTiledSpanMax],
+        s_row_cnt[kTileMax + 2 * kTiledSpanMax];
     __shared__ int s_tile_row_slot[kTileMax], s_tile_row_cnt[kTileMax];
     __shared__ int s_total, s_tile_total;
     __shared__ unsigned long long s_ca, s_cs;
@@ -253,8 +255,8 @@ __global__ void __launch_bounds__(kUpdateThreads) tiled_update(TiledStepArgs a) 
     if (tile >= tiles_x * tiles_y) return;
     const int tx0 = (tile % tiles_x) * te.tx, ty0 = (tile / tiles_x) * te.ty;
     const int tx1 = min(tx0 + te.tx, te.W) - 1, ty1 = min(ty0 + te.ty, te.H) - 1;
-    const int hx0 = max(tx0 - 1, 0), hx1 = min(tx1 + 1, te.W - 1);
-    const int hy0 = max(ty0 - 1, 0), hy1 = min(ty1 + 1, te.H - 1);
+    const int hx0 = max(tx0 - te.span, 0), hx1 = min(tx1 + te.span, te.W - 1);
+    const int hy0 = max(ty0 - te.span, 0), hy1 = min(ty1 + te.span, te.H - 1);
     const int* start = a.start + te.co;
     float4* s_pv = (float4*)smem_raw;
     int* s_id = (int*)(s_pv + a.halo_cap);
