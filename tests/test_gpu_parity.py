@@ -285,6 +285,21 @@ def test_rollout_statistics_within_one_percent(which):
     assert abs(frac - ref["reach_fraction"]) <= max(0.01, 1.0 / ped.sum())
 
 
+@pytest.mark.parametrize("tiled", [False, True])
+def test_non_reactive_robot_teacher_forced(tiled):
+    """robot_responsibility = 1: every pedestrian takes all of the avoidance
+    against the robot, which follows its command (the oracle's closed form of
+    such a pair is pinned on the CPU)."""
+    import dataclasses
+
+    from paper_2505_00690_gb300 import crowd as cw
+
+    sc = dataclasses.replace(scenes.urban_block(7, n_envs=8, steps=40), robot_responsibility=1.0)
+    worst, mism, fb = teacher_forced(sc, 40, flags=cw.CROWD_FLAG_FORCE_TILED if tiled else 0)
+    assert mism == 0
+    assert worst <= VEL_TOL, worst
+
+
 # ----------------------------------------------------------------------------- tiled (global-memory) path
 
 @pytest.mark.parametrize("seed", [0, 1])

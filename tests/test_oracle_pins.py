@@ -176,6 +176,41 @@ def test_head_on_pair_closed_form(half_gap, steps):
         assert (d - 2 * r) / (2 * tau) < s  # the line binds within the compared steps
 
 
+@pytest.mark.parametrize("alpha", [1.0, 0.5])
+def test_robot_pair_closed_form(alpha):
+    """A pedestrian walking at the robot, which moves at its command
+    (-1.4, 0) and does not react.  With the pedestrian's share alpha of the
+    cut-off disk's u = (r/tau - |w|) w_hat, w = v - p/tau, the line bounds its
+    velocity along the axis by v_k - alpha (v_k + 1.4 - (d_k - r)/tau); with
+    alpha = 1 (the robot non-reactive, the pedestrian taking all of the
+    avoidance) that is (d_k - r)/tau - 1.4, independent of v_k, and the gap
+    d - r then shrinks by (1 - dt/tau) every step.  The lateral velocity stays
+    0; d_{k+1} = d_k - dt (v_{k+1} + 1.4)."""
+    r, s, tau, dt, vr = f32(0.3), f32(1.4), 2.0, f32(0.1), f32(1.4)
+    pos = np.array([[0.0, 0.0], [8.0, 0.0]])
+    vel = np.array([[s, 0.0], [-vr, 0.0]])
+    goal = np.array([[100.0, 0.0], [-100.0, 0.0]])
+    sc = dataclasses.replace(one_env(pos, vel, goal, r, s, robot=1, R=15.0, tau=tau, dt=dt),
+                             robot_responsibility=alpha)
+    o = oracle.OracleScene(sc)
+    P, V = sc.pos.astype(np.float64), sc.vel.astype(np.float64)
+    rv = np.array([[-vr, 0.0]], np.float32)
+    d, v = 8.0, float(s)
+    gaps = []
+    for k in range(300):
+        P, V, nb, st = o.step(P, V, rv)
+        v = min(s, v - alpha * (v + vr - (d - 2 * r) / tau))
+        d = d - dt * (v + vr)
+        assert abs(V[0, 0] - v) < 1e-12 and abs(V[0, 1]) < 1e-12, k
+        assert abs(P[1, 0] - P[0, 0] - d) < 1e-10 and np.array_equal(V[1], [-vr, 0.0])
+        gaps.append(d - 2 * r)
+    assert min(gaps) > 0  # never touches
+    if alpha == 1.0:
+        g = np.array(gaps)
+        k0 = int(np.argmax(g < (s + vr) * tau))  # the line binds from here on
+        assert np.allclose(g[k0 + 1:] / g[k0:-1], 1 - dt / tau, rtol=1e-9)
+
+
 # ----------------------------------------------------------------------------- O3 brute force
 
 def _in_vo(v, p, r, tau):
