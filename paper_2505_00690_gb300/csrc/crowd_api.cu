@@ -364,8 +364,8 @@ crowd_status read_err_word(crowd_t h) {
 // which keeps both the (2 span + 1)^2-cell neighbour search and the segment
 // lists exact.
 void build_tiled_env(int e, int base, int n, int seg0, int ns, int robot, const float* pos, const float* radii,
-                     const float* vmax, const float* segs, const crowd_params& p, int co, TiledEnv& te,
-                     std::vector<int>& seg_cell_start, std::vector<int>& seg_cell_ids) {
+                     const float* vmax, const float* segs, const crowd_params& p, int co, bool fine_cells,
+                     TiledEnv& te, std::vector<int>& seg_cell_start, std::vector<int>& seg_cell_ids) {
     const double R = p.neighbor_dist;
     double x0 = 1e300, y0 = 1e300, x1 = -1e300, y1 = -1e300;
     for (int i = 0; i < n; ++i) {
@@ -387,12 +387,12 @@ void build_tiled_env(int e, int base, int n, int seg0, int ns, int robot, const 
     x1 += R;
     y1 += R;
     const double ext = std::max(x1 - x0, y1 - y0);
-    // cells of R / 2 (5 x 5 cells searched, about 30 % fewer candidates than
-    // 3 x 3 cells of R) when a cell still holds every colliding pair, so
-    // that the +-1-cell collision count stays exact
+    // with fine_cells, cells of R / 2 (5 x 5 cells searched, about 30 % fewer
+    // candidates than 3 x 3 cells of R) when a cell still holds every
+    // colliding pair, so that the +-1-cell collision count stays exact
     double rmax = 0.0;
     for (int i = 0; i < n; ++i) rmax = std::max(rmax, (double)radii[base + i]);
-    te.span = R * 0.5 >= 2.0 * rmax ? kTiledSpanMax : 1;
+    te.span = fine_cells && R * 0.5 >= 2.0 * rmax ? kTiledSpanMax : 1;
     const float c = (float)std::max(R * 1.0001 / te.span, ext / (kTiledGridMax - 1));
     te.e = e;
     te.base = base;
@@ -772,11 +772,28 @@ crowd_status crowd_create(int32_t n_envs, const int32_t* agents_per_env, const f
     h->n_tiled = (int)tiled.size();
     std::vector<int> seg_cell_start, seg_cell_ids;
     int total_cells = 0;
+    // Cells of R / 2 cut the instructions of the tiled update by about 14 %
+    // but lengthen each agent's scan (five cell rows instead of three): they
+    // pay when the tiled agents fill the GPU several times over (16 x 20,000
+    // agents: 261 -> 272 M agent-steps/s) and cost a lone 20,000-agent
+    // environment, one partial wave of tiles, 25 % (132 -> 164 us a step).
+    // The neighbour lists, hence the results, are the same either way.
+    long long tiled_agents = 0;
+    for (int e : tiled) tiled_agents += agents_per_env[e];
+    int sm_count = 0;
+    if (!tiled.empty()) {
+        const cudaError_t ea = cudaDeviceGetAttribute(&sm_count, cudaDevAttrMultiProcessorCount, h->device);
+        if (ea != cudaSuccess) {
+            cuda_fail(ea, "device attributes");
+            return bail(CROWD_ECUDA);
+        }
+    }
+    const bool fine_cells = tiled_agents >= (long long)kFineCellRounds * sm_count * kTiledUpdateThreads;
     for (int e : tiled) {
         TiledEnv te{};
         build_tiled_env(e, env_start[e], agents_per_env[e], seg_start[e], segs_per_env ? segs_per_env[e] : 0,
-                        robot[e], init_pos, radii, max_speeds, segments, *p, total_cells, te, seg_cell_start,
-                        seg_cell_ids);
+                        robot[e], init_pos, radii, max_speeds, segments, *p, total_cells, fine_cells, te,
+                        seg_cell_start, seg_cell_ids);
         total_cells += te.W * te.H + 1;
         h->tiled_max_agents = std::max(h->tiled_max_agents, te.n);
         h->tiled_max_tiles = std::max(h->tiled_max_tiles, ((te.W + te.tx - 1) / te.tx) * ((te.H + te.ty - 1) / te.ty));

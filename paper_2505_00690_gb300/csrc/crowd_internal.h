@@ -164,6 +164,11 @@ struct TiledEnv {
 constexpr int kTileMax = 8;
 // Largest neighbour-search span of a tiled environment (cells of R / 2).
 constexpr int kTiledSpanMax = 2;
+// Threads of a CTA of the tiled update kernel.
+constexpr int kTiledUpdateThreads = 256;
+// Cells of R / 2 are used when the tiled agents of a handle number at least
+// this many rounds of kTiledUpdateThreads on every SM.
+constexpr int kFineCellRounds = 4;
 // Agents a tile of the update kernel (256 threads) should hold on average.
 constexpr double kTileFill = 230.0;
 

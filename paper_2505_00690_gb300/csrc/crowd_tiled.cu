@@ -35,7 +35,7 @@ namespace {
 
 constexpr int kCountThreads = 256;
 constexpr int kScanThreads = 1024;
-constexpr int kUpdateThreads = 256;
+constexpr int kUpdateThreads = kTiledUpdateThreads;
 
 __device__ __forceinline__ int clamp_cell(float v, float v0, float inv_c, int n) {
     const int c = __float2int_rd((v - v0) * inv_c);

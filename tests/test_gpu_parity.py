@@ -360,6 +360,24 @@ def test_dense_crowd_full_size_sampled():
     cr.close()
 
 
+def test_tiled_cell_size_and_tiles_change_no_bit():
+    """A 20,000-agent environment stepped alone (cells of R, 4 x 3-cell tiles)
+    and inside the 16-environment crowd (enough agents for cells of R/2 and
+    7 x 7-cell tiles) gives the same bits: the neighbour lists are exact
+    either way and every agent runs the same arithmetic."""
+    from paper_2505_00690_gb300 import crowd as cw
+
+    sc = scenes.dense_crowd(2, steps=4)
+    both = []
+    for scene in (sc.subset([0]), sc):
+        cr = _crowd(scene, cw.CROWD_FLAG_EXPORT_NEIGHBORS)
+        cr.step(n_steps=3)
+        both.append((cr.state()[:20000], cr.neighbors()[:20000]))
+        cr.close()
+    assert np.array_equal(both[0][0], both[1][0])
+    assert np.array_equal(both[0][1], both[1][1])
+
+
 # ----------------------------------------------------------------------------- tuning
 
 def test_tuning_knobs_and_autotune():
