@@ -178,12 +178,14 @@ def test_robot_agent_follows_command():
 # ----------------------------------------------------------------------------- full size, sampled
 
 def test_urban_block_full_size_sampled():
-    """All 256 urban blocks in one launch (the benchmark's configuration):
-    every 100 steps, one step is checked on 2000 sampled agents."""
+    """All 256 urban blocks in one launch, in an autotuned launch shape like
+    the benchmark's: every 100 steps, one step is checked on 2000 sampled
+    agents."""
     from paper_2505_00690_gb300 import crowd as cw
 
     sc = scenes.urban_block(0)
     cr = _crowd(sc, cw.CROWD_FLAG_EXPORT_NEIGHBORS)
+    print("tuning", cr.autotune(n_steps=50))
     o = oracle.OracleScene(sc)
     rng = np.random.default_rng(0)
     k = 0
