@@ -433,7 +433,7 @@ crowd_status crowd_map_sample(const uint8_t* occ, int32_t W, int32_t H, float ce
 const char* crowd_last_error(void);
 
 /* Library ABI version (increments on any signature change). */
-int32_t crowd_abi_version(void);  /* 2 */
+int32_t crowd_abi_version(void);  /* 3: adds crowd_set_episodes */
 
 #ifdef __cplusplus
 }

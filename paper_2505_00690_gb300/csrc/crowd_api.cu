@@ -300,14 +300,14 @@ EpisodeArgs episode_args(crowd_t h) {
     return ep;
 }
 
-// Episodes of the resident environments: environment order[blockIdx.y]
+// Episodes of the resident environments: environment order[blockIdx.x]
 // takes its episode-start rows, goals, goal-queue counters and car arcs when
 // its episode starts at global step `step`.
 __global__ void restart_resident_envs(EpisodeArgs ep, const int* order, const int* env_start, VehicleArgs veh,
                                       float4* state, float2* goal, int* gidx, long long step) {
-    const int e = order[blockIdx.y];
+    const int e = order[blockIdx.x];
     if (!episode_restart(ep.steps[e], step, ep.origin)) return;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = blockIdx.y * blockDim.x + threadIdx.x;
     const int g = env_start[e] + i;
     if (g < env_start[e + 1]) {
         state[g] = ep.state[g];
@@ -516,7 +516,7 @@ crowd_status resident_steps(crowd_t h, float dt, const float2* rv, int n_steps, 
     while (k < n_steps) {
         if (q < starts.size() && starts[q] == k) {
             ++q;
-            restart_resident_envs<<<dim3((span + 255) / 256, h->n_res), 256, 0, s>>>(
+            restart_resident_envs<<<dim3(h->n_res, (span + 255) / 256), 256, 0, s>>>(
                 ep, h->order, h->env_start, veh, h->state, h->goal, h->goal_idx, h->step_index + k);
             CUDA_TRY(cudaGetLastError(), "episode start");
         }
@@ -670,7 +670,7 @@ crowd_status tiled_steps(crowd_t h, float dt, const float2* rv, int n_steps, boo
 
 extern "C" {
 
-int32_t crowd_abi_version(void) { return 2; }
+int32_t crowd_abi_version(void) { return 3; }
 
 const char* crowd_last_error(void) { return g_last_error.c_str(); }
 
