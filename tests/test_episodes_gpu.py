@@ -12,7 +12,8 @@ CROWD_FLAG_FORCE_TILED).
   - statistics count every post-integration state once (an episode's last
     state included, the restored start not), however the steps are split
     into calls, also when the restored start holds overlapping agents;
-  - crowd_set_goals removes the episodes; crowd_reset_stats keeps the clock.
+  - crowd_set_goals removes the episodes; crowd_reset_stats keeps the clock;
+  - cars start over with their environment (arc positions and speeds).
 """
 import numpy as np
 import pytest
@@ -231,3 +232,47 @@ def test_episode_arguments_are_checked():
         cr.set_episodes(np.array([3, 1], np.int32), init_state=bad)
     cr.set_episodes(None)
     cr.close()
+
+
+def test_episodes_with_cars_repeat_and_split_alike():
+    """Cars start over with their environment: arc positions and speeds come
+    back to their values at crowd_set_episodes, so with repeating robot
+    commands the cars' and the crowd's states repeat episode after episode;
+    one call and single steps agree bit for bit."""
+    from paper_2505_00690_gb300 import crowd as cw
+
+    sc, veh = scenes.urban_block_with_vehicles(3, n_envs=4, n_peds=48, n_vehicles=4, steps=40)
+    steps = np.array([6, 0, 9, 4], np.int32)
+    T = 20
+    rv = _periodic_commands(sc, steps, T)
+    runs = []
+    for single in (True, False):
+        cr = cw.Crowd(sc)
+        cr.set_vehicles(veh)
+        cr.set_episodes(steps)
+        seen = [(cr.state(), *cr.vehicle_state())]
+        if single:
+            for t in range(T):
+                cr.step(rv[t:t + 1], n_steps=1)
+                seen.append((cr.state(), *cr.vehicle_state()))
+        else:
+            cr.step(rv, n_steps=T)
+            seen.append((cr.state(), *cr.vehicle_state()))
+        runs.append(seen)
+        cr.close()
+    assert all(np.array_equal(x, y) for x, y in zip(runs[0][-1], runs[1][-1]))
+    states = runs[0]
+    es = sc.env_start
+    car_env = np.searchsorted(es, veh.agent, side="right") - 1
+    for e, L in enumerate(steps):
+        if L == 0:
+            continue
+        rows = slice(es[e], es[e + 1])
+        cars = car_env == e
+        assert cars.any()
+        assert not np.array_equal(states[L][2][cars], states[0][2][cars])  # the cars moved
+        for t in range(L + 1, T + 1):
+            j = (t - 1) % L + 1
+            assert np.array_equal(states[t][0][rows], states[j][0][rows]), (e, t)
+            assert np.array_equal(states[t][1][cars], states[j][1][cars]), (e, t)
+            assert np.array_equal(states[t][2][cars], states[j][2][cars]), (e, t)
