@@ -681,6 +681,7 @@ crowd_status crowd_create(int32_t n_envs, const int32_t* agents_per_env, const f
                           const float* max_speeds, const float* pref_speeds, const float* init_pos,
                           const int32_t* robot_index, const int32_t* segs_per_env, const float* segments,
                           const crowd_params* p, void* cuda_stream, crowd_t* out) {
+    const TraceRange trace("crowd_create");
     if (!out) return fail(CROWD_EINVAL, "out is null");
     *out = nullptr;
     if (!p) return fail(CROWD_EINVAL, "params is null");
@@ -1151,6 +1152,7 @@ crowd_status crowd_read_goal_index(crowd_t h, int32_t* out) {
 }
 
 crowd_status crowd_set_episodes(crowd_t h, const int32_t* steps, const float* init_state, int32_t ptr_kind) {
+    const TraceRange trace("crowd_set_episodes");
     crowd_status st = check_handle(h);
     if (st) return st;
     if (ptr_kind != CROWD_HOST && ptr_kind != CROWD_DEVICE) return fail(CROWD_EINVAL, "ptr_kind must be 0 or 1");
@@ -1212,6 +1214,7 @@ crowd_status crowd_set_state(crowd_t h, const float* state, int32_t ptr_kind) {
 }
 
 crowd_status crowd_step(crowd_t h, float dt, const float* robot_vel, int32_t ptr_kind, int32_t n_steps) {
+    const TraceRange trace("crowd_step");
     crowd_status st = check_handle(h);
     if (st) return st;
     if (!(dt > 0.f) || !std::isfinite(dt)) return fail(CROWD_EINVAL, "dt must be finite and > 0");
@@ -1241,10 +1244,12 @@ crowd_status crowd_step(crowd_t h, float dt, const float* robot_vel, int32_t ptr
     const bool stats = (h->p.flags & CROWD_FLAG_STATS) != 0;
     const float tau_o = h->p.time_horizon_obst > 0.f ? h->p.time_horizon_obst : h->p.time_horizon;
     if (h->n_res) {
+        const TraceRange stage("crowd_step/resident");
         st = resident_steps(h, dt, rv, n_steps, stats, tau_o, h->stream);
         if (st) return st;
     }
     if (h->n_tiled) {
+        const TraceRange stage("crowd_step/tiled");
         st = tiled_steps(h, dt, rv, n_steps, stats, tau_o);
         if (st) return st;
     }
@@ -1253,6 +1258,7 @@ crowd_status crowd_step(crowd_t h, float dt, const float* robot_vel, int32_t ptr
 }
 
 crowd_status crowd_read_state(crowd_t h, float* out, int32_t ptr_kind) {
+    const TraceRange trace("crowd_read_state");
     crowd_status st = check_handle(h);
     if (st) return st;
     if (!out && h->N) return fail(CROWD_EINVAL, "out is null");
@@ -1340,6 +1346,7 @@ crowd_status crowd_set_tuning(crowd_t h, const crowd_tuning* t) {
 }
 
 crowd_status crowd_autotune(crowd_t h, float dt, int32_t n_steps, crowd_tuning* chosen) {
+    const TraceRange trace("crowd_autotune");
     crowd_status st = check_handle(h);
     if (st) return st;
     if (!(dt > 0.f) || !std::isfinite(dt) || n_steps < 1) return fail(CROWD_EINVAL, "dt > 0 and n_steps >= 1 required");

@@ -243,7 +243,19 @@ size_t resident_smem_bytes(int max_agents, int K, int block);
 
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 namespace crowd {
+
+// An NVTX range over a scope of host code (the library's calls and the
+// stages of a step show up by name under a profiler; without one attached a
+// push or pop costs a call that returns).
+struct TraceRange {
+    explicit TraceRange(const char* name) { nvtxRangePushA(name); }
+    ~TraceRange() { nvtxRangePop(); }
+    TraceRange(const TraceRange&) = delete;
+    TraceRange& operator=(const TraceRange&) = delete;
+};
 
 // Host-side construction of the static segment lists (crowd_api.cu).
 double seg_reach(int base, int n, const float* radii, const float* vmax, float tau, float tau_obst);

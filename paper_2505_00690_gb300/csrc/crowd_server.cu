@@ -275,6 +275,7 @@ crowd_status crowd_server_create(const crowd_params* p, float dt, const crowd_se
 }
 
 crowd_status crowd_server_submit(crowd_server_t s, const crowd_request* r, int64_t* id) {
+    const TraceRange trace("crowd_server_submit");
     if (!s || !r || !id) return api_fail(CROWD_EINVAL, "null argument");
     if (s->broken) return api_fail(CROWD_ESTATE, "server is unusable after an earlier CUDA failure");
     const crowd_server_config& c = s->cfg;
@@ -335,6 +336,7 @@ crowd_status crowd_server_submit(crowd_server_t s, const crowd_request* r, int64
 }
 
 crowd_status crowd_server_tick(crowd_server_t s, int32_t* n_live, int32_t* n_finished) {
+    const TraceRange trace("crowd_server_tick");
     if (!s) return api_fail(CROWD_EINVAL, "null server");
     if (s->broken) return api_fail(CROWD_ESTATE, "server is unusable after an earlier CUDA failure");
     const size_t done_before = s->finishing.size();

@@ -225,6 +225,77 @@ def test_env_alone_equals_env_in_batch():
     full.close()
 
 
+@pytest.mark.parametrize("tiled", [False, True])
+def test_checkpoint_resume_equals_continuous_run(tiled):
+    """Checkpoint/resume: the state read after 15 steps, loaded into a new
+    handle (crowd_set_state), continues bit for bit like the run that never
+    stopped; with cars, their arc states are read and written back too."""
+    from paper_2505_00690_gb300 import crowd as cw
+
+    flags = cw.CROWD_FLAG_FORCE_TILED if tiled else 0
+    sc = scenes.urban_block(8, n_envs=8, steps=40)
+    a = _crowd(sc, flags)
+    a.step(sc.robot_vel[:40], n_steps=40)
+    full = a.state()
+    a.close()
+    b = _crowd(sc, flags)
+    b.step(sc.robot_vel[:15], n_steps=15)
+    snap = b.state()
+    b.close()
+    c = _crowd(sc, flags)
+    c.set_state(snap)
+    c.step(sc.robot_vel[15:40], n_steps=25)
+    assert np.array_equal(c.state(), full)
+    c.close()
+    if tiled:
+        return
+    sv, veh = scenes.urban_block_with_vehicles(4, n_envs=4, n_peds=48, n_vehicles=3, steps=40)
+    runs = []
+    for split in (False, True):
+        d = _crowd(sv, 0)
+        d.set_vehicles(veh)
+        if split:
+            d.step(sv.robot_vel[:15], n_steps=15)
+            snap, s, v = d.state(), *d.vehicle_state()
+            d.close()
+            d = _crowd(sv, 0)
+            d.set_vehicles(veh)
+            d.set_state(snap)
+            d.set_vehicle_state(s, v)
+            d.step(sv.robot_vel[15:40], n_steps=25)
+        else:
+            d.step(sv.robot_vel[:40], n_steps=40)
+        runs.append((d.state(), *d.vehicle_state()))
+        d.close()
+    assert all(np.array_equal(x, y) for x, y in zip(*runs))
+
+
+@pytest.mark.parametrize("tiled", [False, True])
+def test_segment_overflow_reported_as_device_error(tiled):
+    """Failure detection without a fault: an agent with more static segments
+    in reach than its line buffer holds (80 short walls on a 2 m ring) keeps
+    the nearest ones, the kernel sets the device error word, the next
+    synchronising call returns CROWD_EDEVICE, and the handle then steps on."""
+    from paper_2505_00690_gb300 import crowd as cw
+
+    ang = np.linspace(0, 2 * np.pi, 80, endpoint=False)
+    segs = [(2 * np.cos(a), 2 * np.sin(a), 2 * np.cos(a + 0.01), 2 * np.sin(a + 0.01)) for a in ang]
+    pos = np.array([[0.0, 0.0], [12.0, 12.0]])
+    sc = one_env(pos, np.zeros((2, 2)), np.array([[0.5, 0.0], [13.0, 12.0]]), 0.3, 1.4, segs=segs)
+    cr = _crowd(sc, cw.CROWD_FLAG_FORCE_TILED if tiled else 0)
+    cr.step(n_steps=1)
+    with pytest.raises(cw.CrowdError) as err:
+        cr.state()
+    assert err.value.status == cw.CROWD_EDEVICE
+    far = sc.state().astype(np.float32)
+    far[0, :2] = [20.0, 20.0]  # away from the ring: nothing overflows
+    cr.set_state(far)
+    cr.step(n_steps=2)
+    out = cr.state()
+    assert np.all(np.isfinite(out))
+    cr.close()
+
+
 def test_multi_step_call_equals_single_steps():
     from paper_2505_00690_gb300 import crowd as cw
 
