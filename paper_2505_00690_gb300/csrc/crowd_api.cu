@@ -1468,6 +1468,7 @@ crowd_status crowd_reset_stats(crowd_t h) {
     if (h->E) CUDA_TRY(cudaMemsetAsync(h->stats, 0, sizeof(EnvStats) * h->E, h->stream), "reset stats");
     h->ep_origin -= h->step_index;  // the episode clock runs on
     h->step_index = 0;
+    if (!h->h_ep_steps.empty()) drop_graph(h);  // cached tiled graphs hold the clock's origin
     return CROWD_OK;
 }
 

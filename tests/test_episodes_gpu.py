@@ -217,6 +217,9 @@ def test_set_goals_removes_episodes_and_reset_stats_keeps_clock(path):
     assert not np.array_equal(straight, plain)
     with_reset = run(lambda c: c.set_episodes(steps), [(3, True), (7, True), (T - 10, False)])
     assert np.array_equal(with_reset, straight)
+    # calls of one length after each reset replay one cached graph on the tiled path
+    same_len = run(lambda c: c.set_episodes(steps), [(5, True), (5, True), (5, False)])
+    assert np.array_equal(same_len, straight)
 
 
 def test_episode_arguments_are_checked():
