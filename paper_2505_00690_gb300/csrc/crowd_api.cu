@@ -482,15 +482,15 @@ crowd_status resident_launch(crowd_t h, float dt, const float2* rv, int n_steps,
 // Steps k in [0, n_steps) of a call at whose start a resident environment
 // starts over (episodes).
 std::vector<int> resident_restart_steps(crowd_t h, int n_steps) {
+    if (h->h_ep_steps.empty()) return {};
     std::vector<char> mark(n_steps, 0);
-    if (!h->h_ep_steps.empty())
-        for (int e : h->h_res_envs) {
-            const long long L = h->h_ep_steps[e];
-            if (L <= 0) continue;
-            const long long t0 = h->step_index - h->ep_origin;  // clock at k = 0
-            long long t = t0 <= 0 ? L : ((t0 + L - 1) / L) * L;
-            for (; t - t0 < n_steps; t += L) mark[t - t0] = 1;
-        }
+    const long long t0 = h->step_index - h->ep_origin;  // clock at k = 0
+    for (int e : h->h_res_envs) {
+        const long long L = h->h_ep_steps[e];
+        if (L <= 0) continue;
+        long long t = t0 <= 0 ? L : ((t0 + L - 1) / L) * L;  // first start at a clock reading > 0
+        for (; t - t0 < n_steps; t += L) mark[t - t0] = 1;
+    }
     std::vector<int> out;
     for (int k = 0; k < n_steps; ++k)
         if (mark[k]) out.push_back(k);
