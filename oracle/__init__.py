@@ -150,16 +150,23 @@ def episode_restarts(t, steps):
     return (st > 0) & (t > 0) & (t % np.maximum(st, 1) == 0)
 
 
+def restart_masked(mask, owner, current, snapshot):
+    """Environments e with mask[e] set start over: the rows of `current`
+    whose environment owner[row] is masked take the rows of `snapshot`; the
+    others are kept.  Returns a new array."""
+    out = np.array(current, copy=True)
+    sel = np.asarray(mask, bool).reshape(-1)[np.asarray(owner, np.int64).reshape(-1)]
+    out[sel] = np.asarray(snapshot)[sel]
+    return out
+
+
 def restart_rows(t, steps, owner, current, snapshot):
     """The rows of `current` whose environment owner[row] starts over at step
     t (episode_restarts) take the rows of `snapshot`; the others are kept.
     Applied at the start of the step, before anything else of it (goal queues,
     cars, the robot command), so the state read after the step that ends an
     episode is that episode's last state.  Returns a new array."""
-    out = np.array(current, copy=True)
-    sel = episode_restarts(t, steps)[np.asarray(owner, np.int64).reshape(-1)]
-    out[sel] = np.asarray(snapshot)[sel]
-    return out
+    return restart_masked(episode_restarts(t, steps), owner, current, snapshot)
 
 
 def rank_key(pi, pj):

@@ -27,6 +27,15 @@ def test_restart_rows_by_hand():
     assert np.array_equal(oracle.restart_rows(5, [2, 0, 3], owner, cur, snap), cur)
 
 
+def test_restart_masked_by_hand():
+    owner = [0, 0, 1, 2, 2]
+    cur = np.arange(5.0)
+    snap = -np.arange(5.0) - 1
+    assert oracle.restart_masked([0, 1, 0], owner, cur, snap).tolist() == [0, 1, -3, 3, 4]
+    assert oracle.restart_masked([1, 0, 1], owner, cur, snap).tolist() == [-1, -2, 2, -4, -5]
+    assert oracle.restart_masked([0, 0, 0], owner, cur, snap).tolist() == cur.tolist()
+
+
 def _run(scene, steps, T, rv):
     """States after 1..T oracle steps from the scene's start, environments
     starting over by `steps`; rv[t] is the robot command of step t."""
