@@ -208,12 +208,21 @@ crowd_status crowd_vehicle_state(crowd_t h, int32_t write, float* s, float* v);
  * state.  Statistics run on across starts: collisions count every
  * post-integration state (episode ends included, restored states not),
  * first-reach steps keep their first value.
- *   steps [n_envs] host, >= 0 (0: never); NULL or all 0 removes the episodes,
- *   as do crowd_set_goals, crowd_set_goal_queue and crowd_set_vehicles.
+ *   steps [n_envs] host, >= 0 (0: never; all 0 keeps the snapshot for
+ *   crowd_restart_envs alone); NULL removes the episodes, as do
+ *   crowd_set_goals, crowd_set_goal_queue and crowd_set_vehicles.
  * crowd_reset_stats leaves the episode clock running.  The serving loop and
  * crowd_step_noalloc have no episodes.  CROWD_EINVAL: steps[e] < 0, NaN/Inf
  * in a host init_state.  Copies; waits for the stream. */
 crowd_status crowd_set_episodes(crowd_t h, const int32_t* steps, const float* init_state, int32_t ptr_kind);
+
+/* Per-environment reset mask: the environments with mask[e] != 0 start over
+ * now, between calls, from the snapshot of crowd_set_episodes (agent rows,
+ * goals, goal-queue counters, car arcs), as a scheduled start does; the
+ * others keep their state.  For episodes that end on events (a collision, an
+ * arrival) rather than after a fixed number of steps.  mask [n_envs] host
+ * (copied).  CROWD_ESTATE without a snapshot; waits for the stream. */
+crowd_status crowd_restart_envs(crowd_t h, const uint8_t* mask);
 
 /* Full state [N][4] (px, py, vx, vy): resume from a checkpoint, or teacher
  * forcing from another simulator's state. */
@@ -433,7 +442,7 @@ crowd_status crowd_map_sample(const uint8_t* occ, int32_t W, int32_t H, float ce
 const char* crowd_last_error(void);
 
 /* Library ABI version (increments on any signature change). */
-int32_t crowd_abi_version(void);  /* 3: adds crowd_set_episodes */
+int32_t crowd_abi_version(void);  /* 3: adds crowd_set_episodes, crowd_restart_envs */
 
 #ifdef __cplusplus
 }

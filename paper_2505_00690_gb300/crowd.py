@@ -30,7 +30,8 @@ EXPORTED = ["crowd_create", "crowd_set_goals", "crowd_set_state", "crowd_step", 
             "crowd_read_neighbors", "crowd_read_stats", "crowd_read_work", "crowd_reset_stats", "crowd_synchronize",
             "crowd_destroy", "crowd_num_agents", "crowd_num_envs", "crowd_last_error", "crowd_abi_version",
             "crowd_get_tuning", "crowd_set_tuning", "crowd_autotune", "crowd_set_goal_queue",
-            "crowd_read_goal_index", "crowd_set_vehicles", "crowd_vehicle_state", "crowd_set_episodes"]
+            "crowd_read_goal_index", "crowd_set_vehicles", "crowd_vehicle_state", "crowd_set_episodes",
+            "crowd_restart_envs"]
 
 
 class CrowdError(RuntimeError):
@@ -77,6 +78,7 @@ def load(path: str = LIB_PATH):
     L.crowd_set_goal_queue.argtypes = [vp, i32, vp, i32, i32]
     L.crowd_read_goal_index.argtypes = [vp, vp]
     L.crowd_set_episodes.argtypes = [vp, vp, vp, i32]
+    L.crowd_restart_envs.argtypes = [vp, vp]
     L.crowd_set_vehicles.argtypes = [vp, i32, vp, vp, i32, vp, vp, vp, vp, vp, C.c_float, C.c_float]
     L.crowd_vehicle_state.argtypes = [vp, i32, vp, vp]
     L.crowd_set_state.argtypes = [vp, vp, i32]
@@ -284,6 +286,12 @@ class Crowd:
         assert init is None or init.shape == (self.N, 4)
         _check(load().crowd_set_episodes(self.h, None if st is None else st.ctypes.data,
                                          None if init is None else init.ctypes.data, CROWD_HOST))
+
+    def restart_envs(self, mask):
+        """Start the environments with mask[e] set over now (see crowd_restart_envs)."""
+        m = np.ascontiguousarray(mask, np.uint8)
+        assert m.shape == (self.E,)
+        _check(load().crowd_restart_envs(self.h, m.ctypes.data))
 
     def set_vehicles(self, veh):
         """Lane-following cars (scenes.Vehicles; see crowd_set_vehicles)."""

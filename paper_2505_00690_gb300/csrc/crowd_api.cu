@@ -89,6 +89,7 @@ struct crowd_ctx {
     float2* ep_goal = nullptr;     // [N] goals at the start of an episode
     int* ep_gidx = nullptr;        // [N] goal-queue counters at the start (with a queue)
     float* ep_veh = nullptr;       // [2V] car arcs at the start (with cars): s | v
+    unsigned char* ep_mask = nullptr;  // [E] environments to start over now (crowd_restart_envs)
     int64_t ep_origin = 0;         // step_index at which the episode clock reads 0
     std::vector<int> h_ep_steps;   // host copy of ep_steps (empty: no episodes)
     // lane-following vehicles (crowd_set_vehicles)
@@ -156,7 +157,7 @@ struct crowd_ctx {
         if (cap_stream) cudaStreamDestroy(cap_stream);
         void* ptrs[] = {env_start, seg_start, robot_index, order, queue, err, state, par, goal, goal_queue, goal_idx,
                         veh_start, veh_agent, veh_lane, veh_s, veh_v, veh_par_a, veh_par_b, lane_pts, lane_start,
-                        lane_cum, veh_pref, ep_steps, ep_state, ep_goal, ep_gidx, ep_veh,
+                        lane_cum, veh_pref, ep_steps, ep_state, ep_goal, ep_gidx, ep_veh, ep_mask,
                         segs, robot_vel, nbr, reach, stats, work, tenvs, state_b, sorted_pv, key, rank,
                         count, start, sorted_id, seg_cell_start, seg_cell_ids, seg_grid, d_step};
         for (void* q : ptrs)
@@ -307,6 +308,28 @@ __global__ void restart_resident_envs(EpisodeArgs ep, const int* order, const in
                                       float4* state, float2* goal, int* gidx, long long step) {
     const int e = order[blockIdx.x];
     if (!episode_restart(ep.steps[e], step, ep.origin)) return;
+    const int i = blockIdx.y * blockDim.x + threadIdx.x;
+    const int g = env_start[e] + i;
+    if (g < env_start[e + 1]) {
+        state[g] = ep.state[g];
+        goal[g] = ep.goal[g];
+        if (ep.gidx) gidx[g] = ep.gidx[g];
+    }
+    if (ep.veh_s) {
+        const int vi = veh.start[e] + i;
+        if (vi < veh.start[e + 1]) {
+            veh.s[vi] = ep.veh_s[vi];
+            veh.v[vi] = ep.veh_v[vi];
+        }
+    }
+}
+
+// Environment blockIdx.x, when mask[e] is set, takes its episode-start rows,
+// goals, goal-queue counters and car arcs (crowd_restart_envs).
+__global__ void restart_masked_envs(EpisodeArgs ep, const unsigned char* mask, const int* env_start, VehicleArgs veh,
+                                    float4* state, float2* goal, int* gidx) {
+    const int e = blockIdx.x;
+    if (!mask[e]) return;
     const int i = blockIdx.y * blockDim.x + threadIdx.x;
     const int g = env_start[e] + i;
     if (g < env_start[e + 1]) {
@@ -670,7 +693,7 @@ crowd_status tiled_steps(crowd_t h, float dt, const float2* rv, int n_steps, boo
 
 extern "C" {
 
-int32_t crowd_abi_version(void) { return 3; }
+int32_t crowd_abi_version(void) { return 3; }  // 3: episodes (crowd_set_episodes, crowd_restart_envs)
 
 const char* crowd_last_error(void) { return g_last_error.c_str(); }
 
@@ -1156,17 +1179,14 @@ crowd_status crowd_set_episodes(crowd_t h, const int32_t* steps, const float* in
     crowd_status st = check_handle(h);
     if (st) return st;
     if (ptr_kind != CROWD_HOST && ptr_kind != CROWD_DEVICE) return fail(CROWD_EINVAL, "ptr_kind must be 0 or 1");
-    bool any = false;
     if (steps)
-        for (int e = 0; e < h->E; ++e) {
+        for (int e = 0; e < h->E; ++e)
             if (steps[e] < 0) return fail(CROWD_EINVAL, "steps[%d] must be >= 0", e);
-            any |= steps[e] > 0;
-        }
     if (init_state && ptr_kind == CROWD_HOST && !finite_all(init_state, (size_t)h->N * 4))
         return fail(CROWD_EINVAL, "init_state holds NaN/Inf");
     CUDA_TRY(cudaStreamSynchronize(h->stream), "synchronize");
     drop_episodes(h);
-    if (!any || h->N == 0) return CROWD_OK;
+    if (!steps || h->N == 0) return CROWD_OK;
     // the episodes exist once every snapshot below is in place
     auto undo = [&](crowd_status s) {
         h->h_ep_steps.assign(1, 0);
@@ -1201,6 +1221,26 @@ crowd_status crowd_set_episodes(crowd_t h, const int32_t* steps, const float* in
     h->h_ep_steps.assign(steps, steps + h->E);
     h->ep_origin = h->step_index;
     drop_graph(h);
+    return CROWD_OK;
+}
+
+crowd_status crowd_restart_envs(crowd_t h, const uint8_t* mask) {
+    const TraceRange trace("crowd_restart_envs");
+    crowd_status st = check_handle(h);
+    if (st) return st;
+    if (!mask) return fail(CROWD_EINVAL, "mask is null");
+    if (h->h_ep_steps.empty()) return fail(CROWD_ESTATE, "no episode snapshot: call crowd_set_episodes first");
+    if (h->N == 0) return CROWD_OK;
+    if (!h->ep_mask) CUDA_TRY(dev_alloc(&h->ep_mask, (size_t)h->E), "allocate restart mask");
+    CUDA_TRY(cudaMemcpyAsync(h->ep_mask, mask, (size_t)h->E, cudaMemcpyHostToDevice, h->stream), "copy restart mask");
+    const VehicleArgs veh{h->n_veh, h->veh_start, h->veh_agent, h->veh_lane, h->veh_s, h->veh_v, h->veh_par_a,
+                          h->veh_par_b, h->lane_pts, h->lane_start, h->lane_cum, h->veh_half_width, h->veh_lookahead};
+    const int span = std::max(h->max_agents, CROWD_MAX_VEHICLES_PER_ENV);
+    restart_masked_envs<<<dim3(h->E, (span + 255) / 256), 256, 0, h->stream>>>(episode_args(h), h->ep_mask, h->env_start,
+                                                                              veh, h->state, h->goal, h->goal_idx);
+    CUDA_TRY(cudaGetLastError(), "restart environments");
+    // the host buffer may be reused once the copy has been made
+    CUDA_TRY(cudaStreamSynchronize(h->stream), "synchronize");
     return CROWD_OK;
 }
 

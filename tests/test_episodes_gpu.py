@@ -279,3 +279,47 @@ def test_episodes_with_cars_repeat_and_split_alike():
             assert np.array_equal(states[t][0][rows], states[j][0][rows]), (e, t)
             assert np.array_equal(states[t][1][cars], states[j][1][cars]), (e, t)
             assert np.array_equal(states[t][2][cars], states[j][2][cars]), (e, t)
+
+
+@pytest.mark.parametrize("path", PATHS)
+def test_restart_mask_starts_chosen_environments_over(path):
+    """crowd_restart_envs: the masked environments take the snapshot's rows
+    and goal counters (the oracle's restart_masked), the others keep theirs,
+    bit for bit.  Stepping on, the masked environments run like a handle of
+    those environments started from the snapshot, the others like a handle
+    that never stopped."""
+    from paper_2505_00690_gb300 import crowd as cw
+
+    sc = scenes.urban_block(9, n_envs=5, n_peds=40, steps=40)
+    queue = scenes.goal_queue(sc, 3, seed=4, hop=2.0)
+    owner = _owner(sc)
+    mask = np.array([1, 0, 1, 0, 1], np.uint8)
+    rv = np.stack([sc.robot_vel_at(t) for t in range(20)]).astype(np.float32)
+    cr = cw.Crowd(sc, flags=_flags(path))
+    with pytest.raises(cw.CrowdError) as err:
+        cr.restart_envs(mask)  # no snapshot yet
+    assert err.value.status == cw.CROWD_ESTATE
+    cr.set_goal_queue(queue, cyclic=True)
+    cr.set_episodes(np.zeros(sc.n_envs, np.int32))  # a snapshot, no scheduled starts
+    snap = cr.state()
+    cr.step(rv[:12], n_steps=12)
+    before, idx_before = cr.state(), cr.goal_index()
+    assert idx_before.any()  # some agents moved on along their queues
+    cr.restart_envs(mask)
+    assert np.array_equal(cr.state(), oracle.restart_masked(mask, owner, before, snap))
+    assert np.array_equal(cr.goal_index(), oracle.restart_masked(mask, owner, idx_before, np.zeros_like(idx_before)))
+    cr.step(rv[12:20], n_steps=8)
+    out = cr.state()
+    cr.close()
+    es = sc.env_start
+
+    def rows(a, envs):
+        return np.concatenate([a[es[e]:es[e + 1]] for e in envs])
+
+    for envs, start, cmds in ((np.flatnonzero(mask), 12, 8), (np.flatnonzero(mask == 0), 0, 20)):
+        sub = cw.Crowd(sc.subset([int(e) for e in envs]), flags=_flags(path))
+        sub.set_goal_queue(rows(queue, envs), cyclic=True)
+        sub.set_state(rows(snap, envs))
+        sub.step(np.ascontiguousarray(rv[start:start + cmds][:, envs]), n_steps=cmds)
+        assert np.array_equal(sub.state(), rows(out, envs)), envs
+        sub.close()
