@@ -15,8 +15,8 @@ paper cites for it (van den Berg et al., ISRR 2011):
   statistics (collision indicator and speed of the paper's metric table,
   Appendix "Evaluation Metrics").
 Around the step: goal queues (advance_goals), episodes that start
-environments over on their own schedules (episode_restarts, restart_rows;
-Sec. 3.3), lane-following cars (``oracle.vehicles``) and the occupancy-map
+environments over on their own schedules or by a mask (episode_restarts,
+restart_rows, restart_masked; Sec. 3.3), lane-following cars (``oracle.vehicles``) and the occupancy-map
 front end (``oracle.frontend``).
 """
 from __future__ import annotations
