@@ -14,7 +14,8 @@ paper cites for it (van den Berg et al., ISRR 2011):
   min-max-penetration fallback, O7 explicit Euler integration, O8 rollout
   statistics (collision indicator and speed of the paper's metric table,
   Appendix "Evaluation Metrics").
-Around the step: goal queues (advance_goals), episodes that start
+Around the step: goal queues (advance_goals), goal pools drawn with
+Philox4x32-10 (advance_goals_pool), episodes that start
 environments over on their own schedules or by a mask (episode_restarts,
 restart_rows, restart_masked; Sec. 3.3), lane-following cars (``oracle.vehicles``) and the occupancy-map
 front end (``oracle.frontend``).
@@ -135,6 +136,41 @@ def advance_goals(pos, radius, goal, idx, queue, cyclic, skip=None):
     k[move] += 1
     rows = np.nonzero(move)[0]
     g[rows] = qu[rows, k[rows] % n_goals]
+    return g, k
+
+
+def advance_goals_pool(pos, radius, goal, idx, pool_start, pool, env_of, seed, skip=None):
+    """Goal pools (a reading: the paper samples agents' start and end points
+    on the traversable ground, Sec. 3.2, and its simulation runs on past an
+    arrival): at the start of a step every agent g (rows of `skip` excepted)
+    within its radius of its goal, decided as advance_goals decides it, draws
+    its next goal from its environment's pool of points: with k = idx[g] the
+    draws it made so far, u = Philox4x32-10(counter (g, k, 0, 0), key (seed
+    low 32 bits, seed high 32 bits)), the pick is floor(u0 * n / 2^32) of the
+    n points of environment env_of[g] (none when n = 0), and idx[g] = k + 1.
+    Returns the new (goal [N][2], idx [N]); the inputs are not modified."""
+    from .frontend import philox4x32_10
+
+    p = np.asarray(pos, np.float64).reshape(-1, 2)
+    g = np.array(goal, np.float64).reshape(-1, 2)
+    k = np.array(idx, np.int64).reshape(-1)
+    ps = np.asarray(pool_start, np.int64).reshape(-1)
+    pl = np.asarray(pool, np.float64).reshape(-1, 2)
+    r = np.asarray(radius, np.float64).reshape(-1)
+    dx = g[:, 0] - p[:, 0]
+    dy = g[:, 1] - p[:, 1]
+    reached = dx * dx + dy * dy <= r * r
+    if skip is not None:
+        reached &= ~np.asarray(skip, bool)
+    key = (int(seed) & 0xFFFFFFFF, (int(seed) >> 32) & 0xFFFFFFFF)
+    for a in np.nonzero(reached)[0]:
+        e = int(env_of[a])
+        n = int(ps[e + 1] - ps[e])
+        if n == 0:
+            continue
+        u0 = philox4x32_10((int(a), int(k[a]), 0, 0), key)[0]
+        g[a] = pl[ps[e] + ((u0 * n) >> 32)]
+        k[a] += 1
     return g, k
 
 
