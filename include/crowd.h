@@ -161,8 +161,24 @@ crowd_status crowd_set_goals(crowd_t h, const float* goals, int32_t ptr_kind);
 #define CROWD_MAX_GOALS 64
 crowd_status crowd_set_goal_queue(crowd_t h, int32_t n_goals, const float* goals, int32_t cyclic, int32_t ptr_kind);
 
-/* Host copy [N] of how many goals each agent has moved past since its queue
- * was set (0 without a queue).  Waits. */
+/* Goal pools (the paper samples agents' start and end points on the
+ * traversable ground, Sec. 3.2; crowd_map_sample draws such points): at the
+ * start of every step an agent (not the robot, not a car) within its radius
+ * of its goal, decided as for goal queues, draws its next goal inside the
+ * kernel from its environment's pool: with k the draws it made so far,
+ * u = Philox4x32-10(counter (g, k, 0, 0), key (seed low 32 bits, seed high
+ * 32 bits)), g its global index, the point floor(u.x n / 2^32) of the n
+ * points of its environment (none drawn when n = 0).
+ *   pool_start [n_envs + 1] host (pool_start[0] = 0, non-decreasing): the
+ *   points of environment e are points[pool_start[e] .. pool_start[e + 1]),
+ *   points [P][2] host.  NULL pool_start removes the pool.
+ * Replaces a goal queue (and crowd_set_goals or crowd_set_goal_queue
+ * replace the pool); the counters restart at 0, current goals stay; removes
+ * the episodes.  CROWD_EINVAL for a bad layout or NaN/Inf.  Copies; waits. */
+crowd_status crowd_set_goal_pool(crowd_t h, const int32_t* pool_start, const float* points, uint64_t seed);
+
+/* Host copy [N] of how many goals each agent has moved past (queue) or drawn
+ * (pool) since they were set (0 without either).  Waits. */
 crowd_status crowd_read_goal_index(crowd_t h, int32_t* out);
 
 /* Lane-following vehicles (the paper's city scenes run cars beside the
@@ -442,7 +458,7 @@ crowd_status crowd_map_sample(const uint8_t* occ, int32_t W, int32_t H, float ce
 const char* crowd_last_error(void);
 
 /* Library ABI version (increments on any signature change). */
-int32_t crowd_abi_version(void);  /* 3: adds crowd_set_episodes, crowd_restart_envs */
+int32_t crowd_abi_version(void);  /* 3: adds crowd_set_episodes, crowd_restart_envs, crowd_set_goal_pool */
 
 #ifdef __cplusplus
 }

@@ -31,7 +31,7 @@ EXPORTED = ["crowd_create", "crowd_set_goals", "crowd_set_state", "crowd_step", 
             "crowd_destroy", "crowd_num_agents", "crowd_num_envs", "crowd_last_error", "crowd_abi_version",
             "crowd_get_tuning", "crowd_set_tuning", "crowd_autotune", "crowd_set_goal_queue",
             "crowd_read_goal_index", "crowd_set_vehicles", "crowd_vehicle_state", "crowd_set_episodes",
-            "crowd_restart_envs"]
+            "crowd_restart_envs", "crowd_set_goal_pool"]
 
 
 class CrowdError(RuntimeError):
@@ -79,6 +79,7 @@ def load(path: str = LIB_PATH):
     L.crowd_read_goal_index.argtypes = [vp, vp]
     L.crowd_set_episodes.argtypes = [vp, vp, vp, i32]
     L.crowd_restart_envs.argtypes = [vp, vp]
+    L.crowd_set_goal_pool.argtypes = [vp, vp, vp, C.c_uint64]
     L.crowd_set_vehicles.argtypes = [vp, i32, vp, vp, i32, vp, vp, vp, vp, vp, C.c_float, C.c_float]
     L.crowd_vehicle_state.argtypes = [vp, i32, vp, vp]
     L.crowd_set_state.argtypes = [vp, vp, i32]
@@ -286,6 +287,16 @@ class Crowd:
         assert init is None or init.shape == (self.N, 4)
         _check(load().crowd_set_episodes(self.h, None if st is None else st.ctypes.data,
                                          None if init is None else init.ctypes.data, CROWD_HOST))
+
+    def set_goal_pool(self, pool_start, points, seed):
+        """Per-environment goal pools (see crowd_set_goal_pool); None removes."""
+        if pool_start is None:
+            _check(load().crowd_set_goal_pool(self.h, None, None, 0))
+            return
+        ps = np.ascontiguousarray(pool_start, np.int32)
+        pts = np.ascontiguousarray(points, np.float32).reshape(-1, 2)
+        assert ps.shape == (self.E + 1,)
+        _check(load().crowd_set_goal_pool(self.h, ps.ctypes.data, pts.ctypes.data, int(seed)))
 
     def restart_envs(self, mask):
         """Start the environments with mask[e] set over now (see crowd_restart_envs)."""

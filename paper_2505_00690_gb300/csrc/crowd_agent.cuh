@@ -16,6 +16,7 @@
 
 #include "crowd_internal.h"
 #include "orca_device.cuh"
+#include "philox.cuh"
 
 namespace crowd {
 
@@ -60,10 +61,20 @@ __device__ __forceinline__ bool goal_reached(float px, float py, float gx, float
     return __dadd_rn(__dmul_rn(ex, ex), __dmul_rn(ey, ey)) <= __dmul_rn(dr, dr);
 }
 
-// Advance agent g (global index) past a reached goal; returns its goal.
-__device__ __forceinline__ float2 advance_goal(const GoalQueue& gq, int g, float4 p, float r, float2 cur) {
-    if (gq.q <= 0 || !goal_reached(p.x, p.y, cur.x, cur.y, r)) return cur;
+// Advance agent g (global index, environment e) past a reached goal; returns
+// its goal.  With a pool the next goal is drawn: with k the draws so far,
+// u = Philox4x32-10(counter (g, k, 0, 0), key seed), point floor(u0 n / 2^32)
+// of the environment's n points.
+__device__ __forceinline__ float2 advance_goal(const GoalQueue& gq, int g, int e, float4 p, float r, float2 cur) {
+    if (!gq.active() || !goal_reached(p.x, p.y, cur.x, cur.y, r)) return cur;
     const int k = gq.idx[g];
+    if (gq.pool_start) {
+        const int b = gq.pool_start[e], n = gq.pool_start[e + 1] - b;
+        if (n <= 0) return cur;
+        const uint4 u = philox4x32_10(make_uint4((unsigned)g, (unsigned)k, 0u, 0u), gq.seed);
+        gq.idx[g] = k + 1;
+        return gq.pool[b + (int)(((unsigned long long)u.x * (unsigned long long)n) >> 32)];
+    }
     if (!gq.cyclic && k + 1 >= gq.q) return cur;  // stays at its last goal
     gq.idx[g] = k + 1;
     return gq.queue[(size_t)g * gq.q + (gq.cyclic ? (k + 1) % gq.q : k + 1)];

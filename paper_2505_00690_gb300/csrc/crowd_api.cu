@@ -83,6 +83,9 @@ struct crowd_ctx {
     float2* goal_queue = nullptr;  // [N][goal_q] (crowd_set_goal_queue)
     int* goal_idx = nullptr;       // [N]
     int goal_q = 0, goal_cyclic = 0;
+    int* pool_start = nullptr;     // [E + 1] goal pool (crowd_set_goal_pool); null: no pool
+    float2* pool = nullptr;        // [P]
+    uint64_t pool_seed = 0;
     size_t goal_queue_cap = 0;     // entries allocated in goal_queue
     int* ep_steps = nullptr;       // [E] episode lengths (crowd_set_episodes); null: no episodes
     float4* ep_state = nullptr;    // [N] agent rows at the start of an episode
@@ -157,7 +160,7 @@ struct crowd_ctx {
         if (cap_stream) cudaStreamDestroy(cap_stream);
         void* ptrs[] = {env_start, seg_start, robot_index, order, queue, err, state, par, goal, goal_queue, goal_idx,
                         veh_start, veh_agent, veh_lane, veh_s, veh_v, veh_par_a, veh_par_b, lane_pts, lane_start,
-                        lane_cum, veh_pref, ep_steps, ep_state, ep_goal, ep_gidx, ep_veh, ep_mask,
+                        lane_cum, veh_pref, ep_steps, ep_state, ep_goal, ep_gidx, ep_veh, ep_mask, pool_start, pool,
                         segs, robot_vel, nbr, reach, stats, work, tenvs, state_b, sorted_pv, key, rank,
                         count, start, sorted_id, seg_cell_start, seg_cell_ids, seg_grid, d_step};
         for (void* q : ptrs)
@@ -346,6 +349,26 @@ __global__ void restart_masked_envs(EpisodeArgs ep, const unsigned char* mask, c
     }
 }
 
+// Goals that move on inside the kernels: a queue or a pool.
+bool goals_move(crowd_t h) { return h->goal_q > 0 || h->pool_start != nullptr; }
+
+GoalQueue goal_args(crowd_t h) {
+    GoalQueue g{h->goal_queue, h->goal_idx, h->goal_q, h->goal_cyclic, h->pool_start, h->pool,
+                make_uint2((unsigned)(h->pool_seed & 0xFFFFFFFFu), (unsigned)(h->pool_seed >> 32))};
+    return g;
+}
+
+// A fixed goal set or a queue replaces a pool.
+void drop_pool(crowd_t h) {
+    if (!h->pool_start) return;
+    cudaStreamSynchronize(h->stream);
+    cudaFree(h->pool_start);
+    cudaFree(h->pool);
+    h->pool_start = nullptr;
+    h->pool = nullptr;
+    drop_graph(h);
+}
+
 crowd_status check_handle(crowd_t h) {
     if (!h) return fail(CROWD_EINVAL, "null handle");
     if (h->broken) return fail(CROWD_ESTATE, "handle is unusable after an earlier CUDA failure");
@@ -468,7 +491,7 @@ crowd_status resident_launch(crowd_t h, float dt, const float2* rv, int n_steps,
     a.seg_cell_ids = h->seg_cell_ids;
     a.par = h->par;
     a.goal = h->goal;
-    a.goals = GoalQueue{h->goal_queue, h->goal_idx, h->goal_q, h->goal_cyclic};
+    a.goals = goal_args(h);
     a.seg_vd = (h->p.flags & CROWD_FLAG_VELOCITY_SEGMENTS) ? 1 : 0;
     a.veh = VehicleArgs{h->n_veh, h->veh_start, h->veh_agent, h->veh_lane, h->veh_s, h->veh_v, h->veh_par_a,
                         h->veh_par_b, h->lane_pts, h->lane_start, h->lane_cum, h->veh_half_width, h->veh_lookahead};
@@ -563,7 +586,7 @@ TiledStepArgs tiled_args(crowd_t h, float dt, const float2* rv, int s, int n_ste
     a.robot_vel = (rv && mode != kTiledStatsOnly) ? rv + (size_t)s * h->E : nullptr;
     a.par = h->par;
     a.goal = h->goal;
-    a.goals = GoalQueue{h->goal_queue, h->goal_idx, h->goal_q, h->goal_cyclic};
+    a.goals = goal_args(h);
     a.ep = episode_args(h);
     a.seg_vd = (h->p.flags & CROWD_FLAG_VELOCITY_SEGMENTS) ? 1 : 0;
     a.segs = h->segs;
@@ -956,6 +979,7 @@ crowd_status crowd_set_goals(crowd_t h, const float* goals, int32_t ptr_kind) {
     if (!goals) return fail(CROWD_EINVAL, "goals is null");
     if (ptr_kind == CROWD_HOST && !finite_all(goals, (size_t)h->N * 2)) return fail(CROWD_EINVAL, "goals hold NaN/Inf");
     drop_episodes(h);
+    drop_pool(h);
     if (h->goal_q) {
         h->goal_q = 0;  // fixed goals replace a goal queue
         drop_graph(h);
@@ -974,6 +998,7 @@ crowd_status crowd_set_goal_queue(crowd_t h, int32_t n_goals, const float* goals
     if (ptr_kind == CROWD_HOST && !finite_all(goals, count * 2)) return fail(CROWD_EINVAL, "goals hold NaN/Inf");
     CUDA_TRY(cudaStreamSynchronize(h->stream), "synchronize");
     drop_episodes(h);
+    drop_pool(h);
     if (h->goal_queue && h->goal_queue_cap < count) {
         cudaFree(h->goal_queue);
         h->goal_queue = nullptr;
@@ -994,6 +1019,42 @@ crowd_status crowd_set_goal_queue(crowd_t h, int32_t n_goals, const float* goals
              "set first goals");
     h->goal_q = n_goals;
     h->goal_cyclic = cyclic ? 1 : 0;
+    drop_graph(h);
+    return CROWD_OK;
+}
+
+crowd_status crowd_set_goal_pool(crowd_t h, const int32_t* pool_start, const float* points, uint64_t seed) {
+    crowd_status st = check_handle(h);
+    if (st) return st;
+    if (pool_start) {
+        if (pool_start[0] != 0) return fail(CROWD_EINVAL, "pool_start[0] must be 0");
+        for (int e = 0; e < h->E; ++e)
+            if (pool_start[e + 1] < pool_start[e]) return fail(CROWD_EINVAL, "pool_start must not decrease");
+        if (pool_start[h->E] > 0 && !points) return fail(CROWD_EINVAL, "points is null");
+        if (pool_start[h->E] > 0 && !finite_all(points, (size_t)pool_start[h->E] * 2))
+            return fail(CROWD_EINVAL, "pool points hold NaN/Inf");
+    }
+    CUDA_TRY(cudaStreamSynchronize(h->stream), "synchronize");
+    drop_episodes(h);  // their snapshot holds the counters of the goals replaced here
+    drop_pool(h);
+    if (!pool_start || h->N == 0) return CROWD_OK;
+    if (h->goal_q) {
+        h->goal_q = 0;  // a pool replaces a goal queue
+        drop_graph(h);
+    }
+    const int P = pool_start[h->E];
+    CUDA_TRY(dev_alloc(&h->pool_start, (size_t)h->E + 1), "allocate goal pool");
+    cudaError_t e = dev_alloc(&h->pool, (size_t)std::max(P, 1));
+    if (e == cudaSuccess) e = cudaMemcpy(h->pool_start, pool_start, sizeof(int) * (h->E + 1), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && P) e = cudaMemcpy(h->pool, points, sizeof(float2) * P, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !h->goal_idx) e = dev_alloc(&h->goal_idx, (size_t)h->N);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->goal_idx, 0, sizeof(int) * h->N, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) {
+        drop_pool(h);
+        return cuda_fail(e, "set goal pool");
+    }
+    h->pool_seed = seed;
     drop_graph(h);
     return CROWD_OK;
 }
@@ -1165,7 +1226,7 @@ crowd_status crowd_read_goal_index(crowd_t h, int32_t* out) {
     if (st) return st;
     if (!out) return fail(CROWD_EINVAL, "out is null");
     if (h->N == 0) return CROWD_OK;
-    if (!h->goal_idx || h->goal_q == 0) {
+    if (!h->goal_idx || !goals_move(h)) {
         std::fill(out, out + h->N, 0);
         return CROWD_OK;
     }
@@ -1196,7 +1257,7 @@ crowd_status crowd_set_episodes(crowd_t h, const int32_t* steps, const float* in
     cudaError_t e = dev_alloc(&h->ep_steps, (size_t)h->E);
     if (e == cudaSuccess) e = dev_alloc(&h->ep_state, (size_t)h->N);
     if (e == cudaSuccess) e = dev_alloc(&h->ep_goal, (size_t)h->N);
-    if (e == cudaSuccess && h->goal_q) e = dev_alloc(&h->ep_gidx, (size_t)h->N);
+    if (e == cudaSuccess && goals_move(h)) e = dev_alloc(&h->ep_gidx, (size_t)h->N);
     if (e == cudaSuccess && h->n_veh) e = dev_alloc(&h->ep_veh, 2 * (size_t)h->n_veh);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(h->ep_steps, steps, sizeof(int) * h->E, cudaMemcpyHostToDevice, h->stream);
@@ -1204,7 +1265,7 @@ crowd_status crowd_set_episodes(crowd_t h, const int32_t* steps, const float* in
         e = cudaMemcpyAsync(h->ep_state, h->state, sizeof(float4) * h->N, cudaMemcpyDeviceToDevice, h->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(h->ep_goal, h->goal, sizeof(float2) * h->N, cudaMemcpyDeviceToDevice, h->stream);
-    if (e == cudaSuccess && h->goal_q)
+    if (e == cudaSuccess && goals_move(h))
         e = cudaMemcpyAsync(h->ep_gidx, h->goal_idx, sizeof(int) * h->N, cudaMemcpyDeviceToDevice, h->stream);
     if (e == cudaSuccess && h->n_veh)
         e = cudaMemcpyAsync(h->ep_veh, h->veh_s, sizeof(float) * h->n_veh, cudaMemcpyDeviceToDevice, h->stream);
@@ -1402,11 +1463,11 @@ crowd_status crowd_autotune(crowd_t h, float dt, int32_t n_steps, crowd_tuning* 
         CUDA_TRY(dev_alloc(&saved, h->N), "autotune scratch");
         cudaError_t e = dev_alloc(&saved_stats, h->E);
         if (e == cudaSuccess) e = dev_alloc(&saved_reach, h->N);
-        if (e == cudaSuccess && h->goal_q) e = dev_alloc(&saved_goal, h->N);
-        if (e == cudaSuccess && h->goal_q) e = dev_alloc(&saved_gidx, h->N);
-        if (e == cudaSuccess && h->goal_q)
+        if (e == cudaSuccess && goals_move(h)) e = dev_alloc(&saved_goal, h->N);
+        if (e == cudaSuccess && goals_move(h)) e = dev_alloc(&saved_gidx, h->N);
+        if (e == cudaSuccess && goals_move(h))
             e = cudaMemcpyAsync(saved_goal, h->goal, sizeof(float2) * h->N, cudaMemcpyDeviceToDevice, h->stream);
-        if (e == cudaSuccess && h->goal_q)
+        if (e == cudaSuccess && goals_move(h))
             e = cudaMemcpyAsync(saved_gidx, h->goal_idx, sizeof(int) * h->N, cudaMemcpyDeviceToDevice, h->stream);
         if (e == cudaSuccess && h->n_veh) e = dev_alloc(&saved_veh, 2 * (size_t)h->n_veh);
         if (e == cudaSuccess && h->n_veh)
@@ -1416,9 +1477,9 @@ crowd_status crowd_autotune(crowd_t h, float dt, int32_t n_steps, crowd_tuning* 
                                 h->stream);
         auto restore_start = [&]() {
             cudaError_t r = cudaMemcpyAsync(h->state, saved, sizeof(float4) * h->N, cudaMemcpyDeviceToDevice, h->stream);
-            if (r == cudaSuccess && h->goal_q)
+            if (r == cudaSuccess && goals_move(h))
                 r = cudaMemcpyAsync(h->goal, saved_goal, sizeof(float2) * h->N, cudaMemcpyDeviceToDevice, h->stream);
-            if (r == cudaSuccess && h->goal_q)
+            if (r == cudaSuccess && goals_move(h))
                 r = cudaMemcpyAsync(h->goal_idx, saved_gidx, sizeof(int) * h->N, cudaMemcpyDeviceToDevice, h->stream);
             if (r == cudaSuccess && h->n_veh)
                 r = cudaMemcpyAsync(h->veh_s, saved_veh, sizeof(float) * h->n_veh, cudaMemcpyDeviceToDevice, h->stream);

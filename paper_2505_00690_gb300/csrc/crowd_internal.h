@@ -7,12 +7,17 @@
 
 namespace crowd {
 
-// Goal queue of a handle (see crowd_set_goal_queue).
+// Goal queue or goal pool of a handle (see crowd_set_goal_queue and
+// crowd_set_goal_pool; at most one of the two is set).
 struct GoalQueue {
     const float2* queue;  // [N][q]
-    int* idx;             // [N] goals reached since the queue was set
+    int* idx;             // [N] goals reached (queue) or drawn (pool) since set
     int q;                // goals per agent (0: no queue)
     int cyclic;           // 1: after the last goal the queue starts again
+    const int* pool_start;  // [E + 1] each environment's points in `pool` (null: no pool)
+    const float2* pool;     // [P] goal points
+    uint2 seed;             // Philox key of the draws
+    __host__ __device__ bool active() const { return q > 0 || pool_start != nullptr; }
 };
 
 // Lane-following vehicles of a handle (see crowd_set_vehicles).

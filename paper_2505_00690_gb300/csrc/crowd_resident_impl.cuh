@@ -550,12 +550,12 @@ __global__ void __launch_bounds__(kMaxThreads, G >= 4 ? 2 : 1) resident_kernel(R
         const int passes = n_steps + (a.stats ? 1 : 0);
         for (int step = 0; step < passes; ++step) {
             const bool compute = step < n_steps;
-            if (compute && a.goals.q > 0) {
+            if (compute && a.goals.active()) {
                 // goal queue: agents within reach of their goal move on to the next
                 for (int i = threadIdx.x; i < c.n; i += blockDim.x) {
                     if (i == c.robot || S.par[i].w != 0.f) continue;
                     const float2 cur = S.goal[i];
-                    const float2 nx = advance_goal(a.goals, c.base + i, S.pv[i], S.par[i].x, cur);
+                    const float2 nx = advance_goal(a.goals, c.base + i, c.e, S.pv[i], S.par[i].x, cur);
                     if (nx.x != cur.x || nx.y != cur.y) {
                         S.goal[i] = nx;
                         a.goal[c.base + i] = nx;

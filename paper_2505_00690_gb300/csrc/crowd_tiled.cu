@@ -66,9 +66,9 @@ __global__ void __launch_bounds__(kCountThreads) tiled_count(TiledStepArgs a) {
         p.w = cmd.y;
         a.state_in[g] = p;
     }
-    if (a.goals.q > 0 && i != te.robot && a.mode != kTiledStatsOnly) {
+    if (a.goals.active() && i != te.robot && a.mode != kTiledStatsOnly) {
         const float2 cur = a.goal[g];
-        const float2 nx = advance_goal(a.goals, g, p, __ldg(&a.par[g]).x, cur);
+        const float2 nx = advance_goal(a.goals, g, te.e, p, __ldg(&a.par[g]).x, cur);
         if (nx.x != cur.x || nx.y != cur.y) a.goal[g] = nx;
     }
     const int k = cell_of(te, p.x, p.y);

@@ -93,6 +93,7 @@ def test_null_handle_calls_fail_cleanly(lib):
     assert lib.crowd_read_goal_index(None, None) == cw.CROWD_EINVAL
     assert lib.crowd_set_episodes(None, None, None, 0) == cw.CROWD_EINVAL
     assert lib.crowd_restart_envs(None, None) == cw.CROWD_EINVAL
+    assert lib.crowd_set_goal_pool(None, None, None, 0) == cw.CROWD_EINVAL
     assert lib.crowd_vehicle_state(None, 0, None, None) == cw.CROWD_EINVAL
     assert lib.crowd_destroy(None) == cw.CROWD_OK
     assert lib.crowd_num_agents(None) == 0

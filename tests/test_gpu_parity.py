@@ -675,6 +675,75 @@ def test_goal_queue_teacher_forced(flags):
     assert worst <= VEL_TOL, worst
 
 
+def _goal_pool(sc, seed=7):
+    """Per-environment goal pools: one point per agent of the environment,
+    drawn like the scene's goals (clear of segments), and first goals within
+    2 m of the starts so that arrivals and draws begin early."""
+    q = scenes.goal_queue(sc, 2, seed=seed)
+    first = (sc.pos + np.clip(q[:, 0] - sc.pos, -2.0, 2.0)).astype(np.float32)
+    return first, np.asarray(sc.env_start, np.int32), np.ascontiguousarray(q[:, 1], np.float32)
+
+
+@pytest.mark.parametrize("flags", [0, 8])
+def test_goal_pool_teacher_forced(flags):
+    """Goal pools drawn inside the kernels with Philox4x32-10: the goal
+    counters and the drawn goals equal the oracle's, neighbours bit-exact,
+    velocities within 1e-4 m/s."""
+    from paper_2505_00690_gb300 import crowd as cw
+
+    sc = scenes.urban_block(5, n_envs=4, steps=150)
+    first, pool_start, pool = _goal_pool(sc)
+    seed = 0x9E3779B97F4A7C15
+    env_of = np.repeat(np.arange(sc.n_envs), sc.agents_per_env)
+    robot_rows = np.zeros(sc.n_agents, bool)
+    for e in range(sc.n_envs):
+        robot_rows[sc.env_start[e] + sc.robot_index[e]] = True
+    cr = _crowd(sc, cw.CROWD_FLAG_EXPORT_NEIGHBORS | flags)
+    cr.set_goals(first)
+    cr.set_goal_pool(pool_start, pool, seed)
+    o = oracle.OracleScene(sc)
+    S = sc.state().astype(np.float32)
+    goal, idx = first.astype(np.float64), np.zeros(sc.n_agents, np.int64)
+    worst, mism, gmis = 0.0, 0, 0
+    for k in range(150):
+        rv = sc.robot_vel_at(k).astype(np.float32)
+        goal, idx = oracle.advance_goals_pool(S[:, :2], sc.radius, goal, idx, pool_start, pool, env_of, seed,
+                                              skip=robot_rows)
+        cr.set_state(S)
+        cr.step(rv[None], n_steps=1)
+        G = cr.state()
+        gmis += int((cr.goal_index() != idx).sum())
+        po, vo, nbO, st = o.step(S[:, :2], S[:, 2:], rv, goal=goal)
+        mism += int(np.any(cr.neighbors() != nbO, axis=1).sum())
+        worst = max(worst, float(np.abs(G[:, 2:].astype(np.float64) - vo).max()))
+        S = np.concatenate([po, vo], 1).astype(np.float32)
+    cr.close()
+    assert idx.sum() > 200, idx.sum()
+    assert gmis == 0 and mism == 0
+    assert worst <= VEL_TOL, worst
+
+
+def test_goal_pool_multi_step_equals_single_steps():
+    from paper_2505_00690_gb300 import crowd as cw
+
+    sc = scenes.urban_block(6, n_envs=4, steps=80)
+    first, pool_start, pool = _goal_pool(sc, seed=3)
+    outs = []
+    for chunks in ((80,), (1,) * 80, (30, 50)):
+        cr = _crowd(sc, 0)
+        cr.set_goals(first)
+        cr.set_goal_pool(pool_start, pool, 12345)
+        k = 0
+        for n in chunks:
+            cr.step(sc.robot_vel[k:k + n], n_steps=n)
+            k += n
+        outs.append((cr.state(), cr.goal_index()))
+        cr.close()
+    assert outs[0][1].sum() > 100
+    for st, gi in outs[1:]:
+        assert np.array_equal(st, outs[0][0]) and np.array_equal(gi, outs[0][1])
+
+
 def test_goal_queue_multi_step_equals_single_steps():
     from paper_2505_00690_gb300 import crowd as cw
 
