@@ -323,3 +323,39 @@ def test_restart_mask_starts_chosen_environments_over(path):
         sub.step(np.ascontiguousarray(rv[start:start + cmds][:, envs]), n_steps=cmds)
         assert np.array_equal(sub.state(), rows(out, envs)), envs
         sub.close()
+
+
+@pytest.mark.parametrize("path", PATHS)
+def test_episodes_with_goal_pools_repeat(path):
+    """A goal pool's draws are counted per agent from the snapshot's counters,
+    so with repeating robot commands an environment draws the same goals in
+    every episode and its states and counters repeat."""
+    from paper_2505_00690_gb300 import crowd as cw
+
+    sc = scenes.urban_block(10, n_envs=3, n_peds=40, steps=40)
+    q = scenes.goal_queue(sc, 2, seed=5)
+    first = (sc.pos + np.clip(q[:, 0] - sc.pos, -1.5, 1.5)).astype(np.float32)
+    steps = np.array([12, 0, 9], np.int32)
+    T = 30
+    rv = _periodic_commands(sc, steps, T)
+    cr = cw.Crowd(sc, flags=_flags(path))
+    cr.set_goals(first)
+    cr.set_goal_pool(np.asarray(sc.env_start, np.int32), np.ascontiguousarray(q[:, 1]), 99)
+    cr.set_episodes(steps)
+    seen = [(cr.state(), cr.goal_index())]
+    for t in range(T):
+        cr.step(rv[t:t + 1], n_steps=1)
+        seen.append((cr.state(), cr.goal_index()))
+    cr.close()
+    es = sc.env_start
+    drew = False
+    for e, L in enumerate(steps):
+        if L == 0:
+            continue
+        rows = slice(es[e], es[e + 1])
+        drew |= bool(seen[L][1][rows].any())
+        for t in range(L + 1, T + 1):
+            j = (t - 1) % L + 1
+            assert np.array_equal(seen[t][0][rows], seen[j][0][rows]), (e, t)
+            assert np.array_equal(seen[t][1][rows], seen[j][1][rows]), (e, t)
+    assert drew  # goals were drawn within the episodes
