@@ -186,9 +186,8 @@ crowd_status crowd_read_goal_index(crowd_t h, int32_t* out);
  * 2000).  Lanes are closed polylines: lane l has points
  * points[lane_start[l]..lane_start[l+1]) ([P][2], at least 2, no zero-length
  * segment; the last point joins the first).  Vehicle k (agents ascending) is
- * crowd agent `agent[k]` (global index, not a robot slot, in an environment
- * stepped by the shared-memory kernel, at most CROWD_MAX_VEHICLES_PER_ENV
- * per environment), on lane `lane[k]` at arc position s[k] in [0, lane
+ * crowd agent `agent[k]` (global index, not a robot slot, at most
+ * CROWD_MAX_VEHICLES_PER_ENV per environment, on either kernel), on lane `lane[k]` at arc position s[k] in [0, lane
  * length) with speed v[k] >= 0, IDM parameters params[k][6] = (desired
  * speed v0, time gap T, acceleration a, comfortable deceleration b, jam
  * distance s0, length), all > 0.  Each step, from the step-start state, a

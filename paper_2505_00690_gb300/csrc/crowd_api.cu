@@ -111,6 +111,7 @@ struct crowd_ctx {
     float veh_half_width = 0.f, veh_lookahead = 0.f;
     std::vector<int> h_env_start;  // [E + 1] host copy
     std::vector<char> h_env_tiled; // [E] environment stepped by the tiled path
+    bool tiled_cars = false;       // some tiled environment has cars
     float4* segs = nullptr;
     float2* robot_vel = nullptr;
     size_t robot_vel_cap = 0;
@@ -588,6 +589,9 @@ TiledStepArgs tiled_args(crowd_t h, float dt, const float2* rv, int s, int n_ste
     a.goal = h->goal;
     a.goals = goal_args(h);
     a.ep = episode_args(h);
+    a.veh = VehicleArgs{h->n_veh, h->veh_start, h->veh_agent, h->veh_lane, h->veh_s, h->veh_v, h->veh_par_a,
+                        h->veh_par_b, h->lane_pts, h->lane_start, h->lane_cum, h->veh_half_width, h->veh_lookahead};
+    a.veh_on = h->tiled_cars ? 1 : 0;
     a.seg_vd = (h->p.flags & CROWD_FLAG_VELOCITY_SEGMENTS) ? 1 : 0;
     a.segs = h->segs;
     a.seg_cell_start = h->seg_cell_start;
@@ -1118,7 +1122,6 @@ crowd_status crowd_set_vehicles(crowd_t h, int32_t n_lanes, const int32_t* lane_
             if (lane[k] < 0 || lane[k] >= n_lanes) return fail(CROWD_EINVAL, "vehicle %d: lane out of range", k);
             const int e = (int)(std::upper_bound(h->h_env_start.begin(), h->h_env_start.end(), agent[k]) -
                                 h->h_env_start.begin()) - 1;
-            if (h->h_env_tiled[e]) return fail(CROWD_EINVAL, "vehicle %d: its environment runs on the tiled path", k);
             if (++per_env[e] > CROWD_MAX_VEHICLES_PER_ENV)
                 return fail(CROWD_EINVAL, "more than %d vehicles in environment %d", CROWD_MAX_VEHICLES_PER_ENV, e);
             int32_t robot = -1;
@@ -1151,6 +1154,8 @@ crowd_status crowd_set_vehicles(crowd_t h, int32_t n_lanes, const int32_t* lane_
             *q = nullptr;
         }
     h->n_veh = 0;
+    h->tiled_cars = false;
+    drop_graph(h);  // cached tiled graphs hold the car arrays
     if (n_vehicles == 0) return CROWD_OK;
     std::vector<int> start(h->E + 1, 0);
     for (int k = 0; k < n_vehicles; ++k) {
@@ -1198,6 +1203,8 @@ crowd_status crowd_set_vehicles(crowd_t h, int32_t n_lanes, const int32_t* lane_
     h->n_veh = n_vehicles;
     h->veh_half_width = half_width;
     h->veh_lookahead = lookahead;
+    for (int e = 0; e < h->E; ++e)
+        if (h->h_env_tiled[e] && start[e + 1] > start[e]) h->tiled_cars = true;
     return CROWD_OK;
 }
 

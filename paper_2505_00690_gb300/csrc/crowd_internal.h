@@ -209,6 +209,8 @@ struct TiledStepArgs {
     float2* goal;             // [N] current goals (advanced in tiled_count with a goal queue)
     GoalQueue goals;
     EpisodeArgs ep;
+    VehicleArgs veh;          // cars (stepped by tiled_vehicles when veh_on)
+    int veh_on;               // some tiled environment has cars
     const float4* segs;
     const int* seg_cell_start;  // [cells + 1 per env] per-cell segment lists
     const int* seg_cell_ids;

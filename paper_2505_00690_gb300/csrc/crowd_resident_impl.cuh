@@ -9,6 +9,7 @@
 #include "crowd_agent.cuh"
 #include "crowd_group.cuh"
 #include "crowd_internal.h"
+#include "crowd_vehicles.cuh"
 #include "orca_device.cuh"
 
 namespace crowd {
@@ -219,6 +220,14 @@ struct SmemAgents {
     __device__ __forceinline__ float4 params(int j) const { return par[j]; }
 };
 
+// The environment's crowd as the car update reads it (shared memory).
+struct SmemCrowd {
+    const float4* pv_;
+    const float4* par_;
+    __device__ __forceinline__ float4 pv(int k) const { return pv_[k]; }
+    __device__ __forceinline__ float4 par(int k) const { return par_[k]; }
+};
+
 // The segment list of the static segment-grid cell holding position `me`.
 __device__ __forceinline__ ListedSegments cell_segments(const ResidentArgs& a, const StepCtx& c, float4 me) {
     const int k = cell_coord(me.y, c.sg.y0, c.sg.inv_c, c.sg.H) * c.sg.W + cell_coord(me.x, c.sg.x0, c.sg.inv_c, c.sg.W);
@@ -283,118 +292,6 @@ __device__ __forceinline__ bool agent_update(const ResidentArgs& a, const AgentP
                                           deferred);
     if (!queued && !deferred) integrate(a, S, c, i, me, pr.x, v, speed_acc);
     return deferred;
-}
-
-// ---- lane-following vehicles (IDM) -------------------------------------
-// Point of lane l (closed polyline) at arc position s.
-__device__ __forceinline__ float2 lane_point(const VehicleArgs& V, int l, float s) {
-    const int p0 = V.lane_start[l], m = V.lane_start[l + 1] - p0;
-    const float* cum = V.cum + p0 + l;
-    int k = 0;
-    while (k + 1 < m && cum[k + 1] <= s) ++k;
-    const float2 a = V.pts[p0 + k], b = V.pts[p0 + (k + 1 == m ? 0 : k + 1)];
-    const float t = (s - cum[k]) / (cum[k + 1] - cum[k]);
-    return make_float2(a.x + t * (b.x - a.x), a.y + t * (b.y - a.y));
-}
-
-// Whether a crowd agent at q (radius r) lies within half_width + r of the
-// lane segment from a along e (length ln), and its arc position there.
-// Near the corridor's edge the distance is taken again in FP64, as the
-// definition evaluates it.
-__device__ __forceinline__ bool lane_blocker(float2 q, float r, float2 a, float2 e, float ln, float c0,
-                                             float half_width, float& s_at) {
-    const float dx = q.x - a.x, dy = q.y - a.y;
-    const float t = fminf(fmaxf((dx * e.x + dy * e.y) / (ln * ln), 0.f), 1.f);
-    const float cx = a.x + t * e.x, cy = a.y + t * e.y;
-    const float lat = sqrtf((q.x - cx) * (q.x - cx) + (q.y - cy) * (q.y - cy));
-    const float thr = half_width + r;
-    bool in = lat <= thr;
-    if (fabsf(lat - thr) <= 1e-4f * thr) {
-        const double ex = e.x, ey = e.y, l2 = (double)ln * (double)ln;
-        const double ddx = (double)q.x - (double)a.x, ddy = (double)q.y - (double)a.y;
-        double td = (ddx * ex + ddy * ey) / l2;
-        td = td < 0.0 ? 0.0 : (td > 1.0 ? 1.0 : td);
-        const double ox = (double)q.x - ((double)a.x + td * ex), oy = (double)q.y - ((double)a.y + td * ey);
-        in = sqrt(ox * ox + oy * oy) <= (double)half_width + (double)r;
-    }
-    s_at = c0 + t * ln;
-    return in;
-}
-
-// IDM step of vehicle vi of the environment held in S (agents [0, n)): the
-// nearest thing ahead on its lane, a car of the lane or a crowd agent within
-// the lane's corridor and `lookahead`, sets the interaction term of
-// a (1 - (v/v0)^4 - (s*/gap)^2), s* = s0 + max(0, v T + v dv / (2 sqrt(a b)));
-// v' = max(0, v + acc dt), s' = s + v' dt wrapped onto the lane.
-__device__ __forceinline__ void idm_vehicle(const VehicleArgs& V, int vi, int v_begin, int v_end, const Smem& S,
-                                            int n, float dt, float& s_new, float& v_new) {
-    const int l = V.lane[vi];
-    const int p0 = V.lane_start[l], m = V.lane_start[l + 1] - p0;
-    const float* cum = V.cum + p0 + l;
-    const float L = cum[m];
-    const float s = V.s[vi], v = V.v[vi];
-    const float4 pa = V.par_a[vi];
-    const float2 pb = V.par_b[vi];
-    float best = INFINITY, gap = 0.f, dv = 0.f;
-    bool has = false;
-    for (int j = v_begin; j < v_end; ++j) {
-        if (j == vi || V.lane[j] != l) continue;
-        float ds = V.s[j] - s;
-        if (ds <= 0.f) ds += L;
-        if (ds < best) {
-            best = ds;
-            gap = ds - 0.5f * (pb.y + V.par_b[j].y);
-            dv = v - V.v[j];
-            has = true;
-        }
-    }
-    for (int k = 0; k < n; ++k) {
-        const float4 pk = S.par[k];
-        if (pk.w != 0.f) continue;  // cars are leaders through their lane only
-        const float4 q = S.pv[k];
-        for (int seg = 0; seg < m; ++seg) {
-            const float2 a = V.pts[p0 + seg], b = V.pts[p0 + (seg + 1 == m ? 0 : seg + 1)];
-            const float2 e = make_float2(b.x - a.x, b.y - a.y);
-            float s_at;
-            if (!lane_blocker(make_float2(q.x, q.y), pk.x, a, e, cum[seg + 1] - cum[seg], cum[seg], V.half_width,
-                              s_at))
-                continue;
-            float ds = s_at - s;
-            if (ds <= 0.f) ds += L;
-            if (ds <= V.lookahead && ds < best) {
-                best = ds;
-                gap = ds - 0.5f * pb.y - pk.x;
-                dv = v;
-                has = true;
-            }
-        }
-    }
-    const float vr = v / pa.x;
-    const float vr2 = vr * vr;
-    const float free_term = 1.f - vr2 * vr2;
-    float acc;
-    if (has) {
-        const float star = pb.x + fmaxf(0.f, v * pa.y + v * dv / (2.f * sqrtf(pa.z * pa.w)));
-        const float q = star / fmaxf(gap, 0.01f);
-        acc = pa.z * (free_term - q * q);
-    } else {
-        acc = pa.z * free_term;
-    }
-    v_new = fmaxf(0.f, v + acc * dt);
-    s_new = s + v_new * dt;
-    if (s_new >= L) s_new -= L;
-}
-
-// Commit the step of car vi: its arc state, and its agent row (position p(s),
-// velocity (p(s') - p(s)) / dt).
-__device__ __forceinline__ void place_vehicle(const VehicleArgs& V, int vi, float s_new, float v_new, float dt,
-                                                  float4* row) {
-    const int l = V.lane[vi];
-    const float2 p_now = lane_point(V, l, V.s[vi]), p_next = lane_point(V, l, s_new);
-    V.s[vi] = s_new;
-    V.v[vi] = v_new;
-    const float inv_dt = 1.f / dt;
-    *row = make_float4(p_now.x, p_now.y, (p_next.x - p_now.x) * inv_dt, (p_next.y - p_now.y) * inv_dt);
 }
 
 // A car's slot in the agent pass (cars are dispatched here by the kernel, so
@@ -567,7 +464,7 @@ __global__ void __launch_bounds__(kMaxThreads, G >= 4 ? 2 : 1) resident_kernel(R
                 const int vb = a.veh.start[c.e], ve = a.veh.start[c.e + 1];
                 const int vi = vb + (int)threadIdx.x;
                 float s_new = 0.f, v_new = 0.f;
-                if (vi < ve) idm_vehicle(a.veh, vi, vb, ve, S, c.n, a.dt, s_new, v_new);
+                if (vi < ve) idm_vehicle(a.veh, vi, vb, ve, SmemCrowd{S.pv, S.par}, c.n, a.dt, s_new, v_new);
                 __syncthreads();
                 if (vi < ve) place_vehicle(a.veh, vi, s_new, v_new, a.dt, S.pv + (a.veh.agent[vi] - c.base));
             }

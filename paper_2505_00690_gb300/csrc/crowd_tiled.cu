@@ -25,8 +25,10 @@
 #include <math.h>
 #include <stdint.h>
 
+#include "../../include/crowd.h"
 #include "crowd_agent.cuh"
 #include "crowd_internal.h"
+#include "crowd_vehicles.cuh"
 #include "orca_device.cuh"
 
 namespace crowd {
@@ -52,11 +54,15 @@ __global__ void __launch_bounds__(kCountThreads) tiled_count(TiledStepArgs a) {
     if (i >= te.n) return;
     const int g = te.base + i;
     float4 p = a.state_in[g];
+    const bool car = __ldg(&a.par[g]).w != 0.f;
     if (a.mode != kTiledStatsOnly && a.ep.steps && episode_restart(a.ep.steps[te.e], *a.step_index, a.ep.origin)) {
         // episodes: the environment starts over (the host counted the
-        // statistics of the episode's last state before this step)
-        p = a.ep.state[g];
-        a.state_in[g] = p;
+        // statistics of the episode's last state before this step); a car's
+        // row was placed from its restored arc by tiled_vehicles already
+        if (!car) {
+            p = a.ep.state[g];
+            a.state_in[g] = p;
+        }
         a.goal[g] = a.ep.goal[g];
         if (a.ep.gidx) a.goals.idx[g] = a.ep.gidx[g];
     }
@@ -66,7 +72,7 @@ __global__ void __launch_bounds__(kCountThreads) tiled_count(TiledStepArgs a) {
         p.w = cmd.y;
         a.state_in[g] = p;
     }
-    if (a.goals.active() && i != te.robot && a.mode != kTiledStatsOnly) {
+    if (a.goals.active() && i != te.robot && !car && a.mode != kTiledStatsOnly) {
         const float2 cur = a.goal[g];
         const float2 nx = advance_goal(a.goals, g, te.e, p, __ldg(&a.par[g]).x, cur);
         if (nx.x != cur.x || nx.y != cur.y) a.goal[g] = nx;
@@ -215,7 +221,7 @@ __device__ __forceinline__ void tile_agent(const TiledStepArgs& a, const AgentPa
             if (s < ap.K) out[s] = s < nb.cnt ? nb.id[s] : -1;
     }
     float2 v;
-    if (i == te.robot) {
+    if (i == te.robot || pr.w != 0.f) {  // the robot and the cars move as commanded
         v = make_float2(me.z, me.w);
     } else {
         // segment candidates: the cell's precomputed list
@@ -232,7 +238,7 @@ __device__ __forceinline__ void tile_agent(const TiledStepArgs& a, const AgentPa
     nx.z = v.x;
     nx.w = v.y;
     a.state_out[g] = nx;
-    if (a.stats && i != te.robot) {
+    if (a.stats && i != te.robot && pr.w == 0.f) {
         speed += (double)sqrtf(v.x * v.x + v.y * v.y);
         const float2 gl = __ldg(&a.goal[g]);
         const float gx = gl.x - nx.x, gy = gl.y - nx.y;
@@ -333,6 +339,58 @@ __global__ void __launch_bounds__(kUpdateThreads) tiled_update(TiledStepArgs a) 
     }
 }
 
+constexpr int kVehicleThreads = 256;
+
+// Cars of tiled environment blockIdx.x (at most CROWD_MAX_VEHICLES_PER_ENV),
+// ahead of the step's other kernels.  All threads: for every (car, crowd
+// agent) pair, the distance ahead on the car's lane when the agent blocks
+// it, reduced per car to the smallest (distance, agent index), the order the
+// sequential scan keeps, by a shared 64-bit minimum.  One thread per car:
+// the IDM step from the step-start state.  Then the arcs and the cars'
+// agent rows are committed.  An environment that starts over at this step
+// gives its cars their snapshot arcs and shows them the snapshot's crowd
+// (which tiled_count restores right after).
+__global__ void __launch_bounds__(kVehicleThreads) tiled_vehicles(TiledStepArgs a) {
+    __shared__ unsigned long long s_best[CROWD_MAX_VEHICLES_PER_ENV];
+    const TiledEnv te = a.envs[blockIdx.x];
+    const VehicleArgs V = a.veh;
+    const int vb = V.start[te.e], nv = min(V.start[te.e + 1] - vb, CROWD_MAX_VEHICLES_PER_ENV);
+    if (nv <= 0) return;
+    const bool restart = a.ep.steps && episode_restart(a.ep.steps[te.e], *a.step_index, a.ep.origin);
+    const int t = threadIdx.x;
+    if (t < nv) {
+        s_best[t] = ~0ull;
+        if (restart && a.ep.veh_s) {
+            V.s[vb + t] = a.ep.veh_s[vb + t];
+            V.v[vb + t] = a.ep.veh_v[vb + t];
+        }
+    }
+    __syncthreads();
+    const float4* rows = (restart ? a.ep.state : a.state_in) + te.base;
+    const float4* par = a.par + te.base;
+    for (int k = t; k < te.n; k += blockDim.x) {
+        const float4 pk = __ldg(&par[k]);
+        if (pk.w != 0.f) continue;  // cars are leaders through their lane only
+        const float4 q = rows[k];
+        for (int c = 0; c < nv; ++c) {
+            float ds;
+            if (agent_ahead(V, vb + c, make_float2(q.x, q.y), pk.x, ds))
+                atomicMin(&s_best[c], ((unsigned long long)__float_as_uint(ds) << 32) | (unsigned)k);
+        }
+    }
+    __syncthreads();
+    float s_new = 0.f, v_new = 0.f;
+    if (t < nv) {
+        const unsigned long long b = s_best[t];
+        const bool blocked = b != ~0ull;
+        const float ds = blocked ? __uint_as_float((unsigned)(b >> 32)) : INFINITY;
+        const float r = blocked ? __ldg(&par[(int)(unsigned)(b & 0xFFFFFFFFull)]).x : 0.f;
+        idm_with_blocker(V, vb + t, vb, vb + nv, ds, r, a.dt, s_new, v_new);
+    }
+    __syncthreads();
+    if (t < nv) place_vehicle(V, vb + t, s_new, v_new, a.dt, a.state_in + V.agent[vb + t]);
+}
+
 __global__ void tiled_finish_step(TiledStepArgs a) {
     // one thread: count the step in the statistics and advance the step index
     if (a.stats && a.mode != kTiledStatsOnly)
@@ -369,6 +427,7 @@ cudaError_t tiled_init(int halo_cap) {
 cudaError_t launch_tiled_step(const TiledStepArgs& a, int max_agents, int max_tiles, cudaStream_t s) {
     if (a.n_envs == 0) return cudaSuccess;
     const dim3 agrid((max_agents + kCountThreads - 1) / kCountThreads, a.n_envs);
+    if (a.veh_on && a.mode != kTiledStatsOnly) tiled_vehicles<<<a.n_envs, kVehicleThreads, 0, s>>>(a);
     tiled_count<<<agrid, kCountThreads, 0, s>>>(a);
     tiled_scan<<<a.n_envs, kScanThreads, 0, s>>>(a);
     tiled_scatter<<<agrid, kCountThreads, 0, s>>>(a);

@@ -237,7 +237,8 @@ def test_episode_arguments_are_checked():
     cr.close()
 
 
-def test_episodes_with_cars_repeat_and_split_alike():
+@pytest.mark.parametrize("path", PATHS)
+def test_episodes_with_cars_repeat_and_split_alike(path):
     """Cars start over with their environment: arc positions and speeds come
     back to their values at crowd_set_episodes, so with repeating robot
     commands the cars' and the crowd's states repeat episode after episode;
@@ -250,7 +251,7 @@ def test_episodes_with_cars_repeat_and_split_alike():
     rv = _periodic_commands(sc, steps, T)
     runs = []
     for single in (True, False):
-        cr = cw.Crowd(sc)
+        cr = cw.Crowd(sc, flags=_flags(path))
         cr.set_vehicles(veh)
         cr.set_episodes(steps)
         seen = [(cr.state(), *cr.vehicle_state())]

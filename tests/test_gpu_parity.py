@@ -852,18 +852,20 @@ def _vehicle_oracle_step(sc, veh, lanes, S, vs, vv):
     return s_new, v_new, S
 
 
-def test_vehicles_teacher_forced():
+@pytest.mark.parametrize("tiled", [False, True])
+def test_vehicles_teacher_forced(tiled):
     """Urban blocks with ring-road cars: the host runs the cars' IDM and the
     crowd step of the oracle from the teacher state (cars as vehicles), the
-    GPU does both inside its step; car arc positions and speeds, pedestrian
-    velocities (1e-4) and neighbour lists (bit-exact) agree."""
+    GPU does both inside its step, on either kernel; car arc positions and
+    speeds, pedestrian velocities (1e-4) and neighbour lists (bit-exact)
+    agree."""
     from oracle import vehicles as VH
     from paper_2505_00690_gb300 import crowd as cw
 
     sc, veh = scenes.urban_block_with_vehicles(2, n_envs=6, n_peds=96, n_vehicles=5, steps=120)
     lanes = VH.Lanes(veh.points, veh.lane_start)
     kind = _vehicle_kind(sc, veh)
-    cr = _crowd(sc, cw.CROWD_FLAG_EXPORT_NEIGHBORS)
+    cr = _crowd(sc, cw.CROWD_FLAG_EXPORT_NEIGHBORS | (cw.CROWD_FLAG_FORCE_TILED if tiled else 0))
     cr.set_vehicles(veh)
     o = oracle.OracleScene(sc)
     S = sc.state().astype(np.float32)
@@ -893,6 +895,26 @@ def test_vehicles_teacher_forced():
     assert worst_ped <= VEL_TOL, worst_ped
     assert worst_car <= VEL_TOL, worst_car
     assert stopped > 0  # some cars had to stop for pedestrians on the road
+
+
+def test_vehicles_tiled_multi_step_equals_single_steps():
+    """Cars on the tiled path: a graph-replayed multi-step call equals single
+    steps and other splits, bit for bit."""
+    from paper_2505_00690_gb300 import crowd as cw
+
+    sc, veh = scenes.urban_block_with_vehicles(3, n_envs=4, n_peds=64, n_vehicles=4, steps=60)
+    outs = []
+    for chunks in ((60,), (1,) * 60, (25, 35)):
+        cr = _crowd(sc, cw.CROWD_FLAG_FORCE_TILED)
+        cr.set_vehicles(veh)
+        k = 0
+        for n in chunks:
+            cr.step(sc.robot_vel[k:k + n], n_steps=n)
+            k += n
+        outs.append((cr.state(), *cr.vehicle_state()))
+        cr.close()
+    for st, s_, v_ in outs[1:]:
+        assert np.array_equal(st, outs[0][0]) and np.array_equal(s_, outs[0][1]) and np.array_equal(v_, outs[0][2])
 
 
 def test_vehicles_multi_step_equals_single_steps_and_autotune_restores():
