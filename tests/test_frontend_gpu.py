@@ -119,3 +119,46 @@ def test_front_end_feeds_the_crowd_step(torch):
         S = np.concatenate([po, vo], 1).astype(np.float32)
     cr.close()
     assert worst <= 1e-4, worst
+
+
+def test_map_to_crowd_pipeline(torch):
+    """The paper's pipeline on one environment (Sec. 3.2): an occupancy map
+    -> its boundary segments and start points sampled on free cells with a
+    clearance (front end) -> a crowd whose goals are drawn inside the step
+    from a pool of free-cell samples -> 200 steps: every agent's centre stays
+    on free ground, goals are drawn, and the run equals single steps."""
+    from paper_2505_00690_gb300 import crowd as cw
+    from paper_2505_00690_gb300 import frontend as FE
+    from paper_2505_00690_gb300.scenes import Scene
+
+    H, W, cell = 40, 40, 0.5
+    occ = np.zeros((H, W), np.uint8)
+    occ[6:12, 8:22] = 1
+    occ[20:34, 26:31] = 1
+    occ[25:29, 4:16] = 1
+    occ_t = torch.from_numpy(occ).cuda()
+    segs = FE.map_segments(occ_t, cell).cpu().numpy()
+    starts = FE.map_sample(occ_t, cell, 48, clearance=2, seed=11, stream_id=0)[0].cpu().numpy()
+    pool = FE.map_sample(occ_t, cell, 200, clearance=2, seed=11, stream_id=1)[0].cpu().numpy()
+    n = len(starts)
+    sc = Scene(name="map", agents_per_env=np.array([n], np.int32), radius=np.full(n, 0.2, np.float32),
+               max_speed=np.full(n, 1.2, np.float32), pref_speed=np.full(n, 1.2, np.float32), pos=starts,
+               vel=np.zeros((n, 2), np.float32), goal=starts.copy(), robot_index=np.array([-1], np.int32),
+               segs_per_env=np.array([len(segs)], np.int32), segments=segs.astype(np.float32), tau=2.0,
+               tau_obst=2.0, neighbor_dist=3.0, max_neighbors=10, dt=0.1)
+    outs = []
+    for chunks in ((200,), (1,) * 200):
+        cr = cw.Crowd(sc)
+        cr.set_goal_pool(np.array([0, len(pool)], np.int32), pool, seed=5)
+        for k in chunks:
+            cr.step(n_steps=k)
+        outs.append((cr.state(), cr.goal_index()))
+        cr.close()
+    (S, drawn), (S1, drawn1) = outs
+    assert np.array_equal(S, S1) and np.array_equal(drawn, drawn1)
+    assert drawn.sum() > n  # every agent arrives at least about once and draws again
+    cx = np.floor(S[:, 0] / cell).astype(int)
+    cy = np.floor(S[:, 1] / cell).astype(int)
+    inside = (cx >= 0) & (cx < W) & (cy >= 0) & (cy < H)
+    assert inside.all()
+    assert (occ[cy, cx] == 0).all()
