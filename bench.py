@@ -40,7 +40,7 @@ ROLLOUT = 1000
 # dram__bytes_read.sum + dram__bytes_write.sum of one 1000-step rollout launch of
 # the resident kernel (ncu, `bench.py --profile-case rollout`, one pass); taken
 # again whenever the kernel changes
-ROLLOUT_DRAM_BYTES = 22.56e6
+ROLLOUT_DRAM_BYTES = 22.49e6
 FP32_LANES_PER_SM = 128
 N_SMS = 152
 
