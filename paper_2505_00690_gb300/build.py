@@ -18,8 +18,11 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libcrowd.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+# -ftz=true: FP32 denormals flush to zero (every FP32 quantity of the step is
+# far above 1e-38); it saved the spills of the one-lane kernel and ran the
+# urban block 5 % and the other workloads 2-3 % faster
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
-              "-prec-div=false", "-prec-sqrt=false",
+              "-prec-div=false", "-prec-sqrt=false", "-ftz=true",
               "-I", INCLUDE, "-I", CSRC]
 
 
