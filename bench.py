@@ -38,9 +38,12 @@ UNIT = "agent-steps/s"
 WORKLOAD = "urban_block: 256 envs x (128 peds + 1 robot), 40x40 m, 36 segments/env, 1000-step rollout, dt 0.1"
 ROLLOUT = 1000
 # dram__bytes_read.sum + dram__bytes_write.sum of one 1000-step rollout launch of
-# the resident kernel (ncu, `bench.py --profile-case rollout`, one pass); taken
-# again whenever the kernel changes
-ROLLOUT_DRAM_BYTES = 22.49e6
+# the resident kernel (ncu, `bench.py --profile-case rollout`, one pass), or None
+# when the kernel has changed since the counters were taken: the last capture
+# (22.49e6 B) predates the flush-to-zero build, so `traffic` is null and that
+# capture is reported beside it as `traffic_last_capture`
+ROLLOUT_DRAM_BYTES = None
+ROLLOUT_DRAM_BYTES_LAST_CAPTURE = {"bytes": 22.49e6, "build": "before -ftz=true"}
 FP32_LANES_PER_SM = 128
 N_SMS = 152
 
@@ -233,6 +236,7 @@ def run_ours(args):
     achieved = flops / launch_s / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
                 "frac": achieved / fp32_peak, "traffic": ROLLOUT_DRAM_BYTES,
+                "traffic_last_capture": ROLLOUT_DRAM_BYTES_LAST_CAPTURE,
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz max SM clock",
                 "flops_per_launch": flops, "work_per_agent_step": {k: v / max(1, work["agent_steps"])
                                                                    for k, v in work.items() if k != "agent_steps"}}
