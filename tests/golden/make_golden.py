@@ -3,6 +3,7 @@
 generator are called; the fixtures pin the oracle against later changes of
 its arithmetic (a change that moves them must say, in its commit, which
 reading of the paper justifies it)."""
+import dataclasses
 import os
 import sys
 
@@ -20,6 +21,9 @@ CASES = {
                                           "plain square, seed 0: 32 agents, 20 x 20 m, no obstacles"),
     "oracle_urban_block_seed1_env0_8steps": (lambda: scenes.urban_block(1, n_envs=1, steps=8), 8,
                                              "urban block, seed 1, one environment: 128 pedestrians, a robot, 36 walls"),
+    "oracle_urban_block_seed2_env0_8steps_vd": (
+        lambda: dataclasses.replace(scenes.urban_block(2, n_envs=1, steps=8), segment_mode=1), 8,
+        "urban block, seed 2, one environment, velocity-dependent segment half-planes"),
 }
 
 

@@ -26,7 +26,8 @@ def test_philox_known_answer_vectors():
         assert F.philox4x32_10(w[0:4], w[4:6]) == tuple(w[6:10])
 
 
-@pytest.mark.parametrize("name", ["oracle_plain_square_seed0_10steps", "oracle_urban_block_seed1_env0_8steps"])
+@pytest.mark.parametrize("name", ["oracle_plain_square_seed0_10steps", "oracle_urban_block_seed1_env0_8steps",
+                                  "oracle_urban_block_seed2_env0_8steps_vd"])
 def test_oracle_reproduces_its_fixture(name):
     import importlib.util
 
