@@ -1,18 +1,24 @@
 """Benchmark of the batched ORCA crowd step (agent-steps/s).
 
-Workload: 256 urban blocks (40 x 40 m, 8 rectangular buildings + 4 sidewalk
-edges = 36 segments each), 128 pedestrians + 1 robot agent per block, robot
-commands from a seeded action tensor, 1000-step rollouts, dt 0.1 s, tau 2 s,
-R 5 m, K 10.  One benchmark step = one full 1000-step rollout of all 256
-blocks from the initial state (33,024 agents x 1000 steps), issued as one
-``crowd_step(n_steps=1000)`` call.
+Headline workload (the largest single-GPU configuration): the dense crowd,
+16 environments x 20,000 pedestrians at 2 per m^2 in 100 x 100 m with 200
+random segment obstacles each, K = 16 neighbours within R = 3 m, dt 0.1 s.
+One benchmark step = one 500-step rollout of all 16 environments from the
+initial state (320,000 agents x 500 steps), issued as one
+``crowd_step(n_steps=500)`` call (graph-replayed tiled kernels).
 
 Timed region: the K rollouts, each bracketed by CUDA events on the crowd
 stream; between rollouts (untimed) the state is reset on the device and a
 256 MiB buffer is written to flush L2.  ``e2e`` repeats the measurement
-through the C ABI with host buffers: per step the initial state and the
-robot commands go host->device from pinned memory and the final state comes
-back device->host, all inside the timed region.
+through the C ABI with host buffers: per step the initial state goes
+host->device from pinned memory and the final state comes back
+device->host, inside the timed region.
+
+The same line carries the serving workload (Poisson request stream at
+200 req/s: p50/p99 latency and throughput, plus a sweep of arrival rates),
+the urban block and the uneven batch (batched and plain forms), the plain
+form of the headline, the CPU oracle on the host cores, the roofline of the
+update kernel and the sampled clocks.
 
 ``--impl reference`` times the FP64 CPU oracle (the parity reference) on a
 bounded sample of the same workload on the host cores.
@@ -22,6 +28,7 @@ from __future__ import annotations
 import argparse
 import json
 import os
+import socket
 import subprocess
 import sys
 import tempfile
@@ -35,17 +42,16 @@ if ROOT not in sys.path:
 
 METRIC = "agent-steps/sec at <=1e-4 m/s vs FP64 oracle, batched vs plain; p50/p99 latency"
 UNIT = "agent-steps/s"
-WORKLOAD = "urban_block: 256 envs x (128 peds + 1 robot), 40x40 m, 36 segments/env, 1000-step rollout, dt 0.1"
-ROLLOUT = 1000
-# dram__bytes_read.sum + dram__bytes_write.sum of one 1000-step rollout launch of
-# the resident kernel (ncu, `bench.py --profile-case rollout`, one pass), or None
-# when the kernel has changed since the counters were taken: the last capture
-# (22.49e6 B) predates the flush-to-zero build, so `traffic` is null and that
-# capture is reported beside it as `traffic_last_capture`
-ROLLOUT_DRAM_BYTES = None
-ROLLOUT_DRAM_BYTES_LAST_CAPTURE = {"bytes": 22.49e6, "build": "before -ftz=true"}
+WORKLOAD = ("dense_crowd: 16 envs x 20,000 pedestrians (2 per m^2 in 100x100 m, 200 segments/env), K 16, "
+            "R 3 m, 500-step rollout, dt 0.1")
+ROLLOUT = 500
+# dram__bytes_read.sum + dram__bytes_write.sum of one launch of the update
+# kernel on this workload (ncu, one pass, `bench.py --profile-case dense`),
+# or None when the kernel has changed since the counters were taken
+UPDATE_DRAM_BYTES = None
 FP32_LANES_PER_SM = 128
 N_SMS = 152
+SERVE_RATES = (200.0, 400.0, 800.0, 1600.0)
 
 
 def _dist_env():
@@ -109,21 +115,101 @@ class Clocks:
                 "samples": len(sm)}
 
 
-def measured_peaks():
-    try:
-        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except Exception:
-        return None
-
-
 def algorithmic_flops(work):
     """Algorithmic FP32 operations of the counted work (per-unit costs of the
-    crowd step: 7 per neighbour candidate, 35 per agent half-plane, 20 per
-    segment half-plane, 12 per segment distance test, 4 per LP check, 15 + 10k
-    per 1D sub-solve scanning k previous lines)."""
+    crowd step: 7 per neighbour candidate tested, 35 per agent half-plane,
+    20 per segment half-plane, 12 per segment distance test, 4 per LP check,
+    15 + 10k per 1D sub-solve scanning k previous lines)."""
     return (7 * work["candidates"] + 35 * work["agent_lines"] + 20 * work["obstacle_lines"]
             + 12 * work["segment_tests"] + 4 * work["lp_checks"] + 15 * work["lp_solves"]
             + 10 * work["lp_solve_lines"])
+
+
+def time_rollouts(cr, rv_dev, init, steps, n_timed, n_warm, stream, flush, dist=False):
+    """Rollouts from `init` of `steps` steps: n_warm untimed, then n_timed each
+    bracketed by CUDA events on the crowd stream (state reset and L2 flush
+    between them, untimed).  Returns (per-rollout ms, wall seconds, kernels
+    the library launched in the timed region)."""
+    import torch
+
+    def reset():
+        cr.set_state(init)
+        with torch.cuda.stream(stream):
+            flush.fill_(1.0)
+
+    for _ in range(n_warm):
+        reset()
+        cr.step(rv_dev, n_steps=steps)
+    torch.cuda.synchronize()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(n_timed)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(n_timed)]
+    if dist:
+        import torch.distributed as tdist
+
+        tdist.barrier()
+    torch.cuda.synchronize()
+    launches0 = cr.launches()
+    t0 = time.perf_counter()
+    for k in range(n_timed):
+        reset()
+        starts[k].record(stream)
+        cr.step(rv_dev, n_steps=steps)
+        ends[k].record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    launches = cr.launches() - launches0
+    if dist:
+        tdist.barrier()
+    return [s.elapsed_time(e) for s, e in zip(starts, ends)], wall, launches
+
+
+def plain_form(sc, steps, max_envs, stream):
+    """The plain form: the same kernels, one environment per launch and one
+    step per launch, on the first max_envs environments."""
+    import torch
+
+    from paper_2505_00690_gb300 import crowd as cw
+
+    envs = list(range(min(sc.n_envs, max_envs)))
+    handles = [cw.Crowd(sc.subset([e]), flags=0, stream=stream.cuda_stream) for e in envs]
+    rvs = [None if sc.robot_vel is None else
+           torch.from_numpy(np.ascontiguousarray(sc.robot_vel[:steps, e:e + 1])).cuda() for e in envs]
+    for h, rv in zip(handles, rvs):  # warm
+        h.step(None if rv is None else rv[:1], n_steps=1)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(steps):
+        for h, rv in zip(handles, rvs):
+            h.step(None if rv is None else rv[k:k + 1], n_steps=1)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    agents = sum(int(sc.agents_per_env[e]) for e in envs)
+    for h in handles:
+        h.close()
+    return {"value": agents * steps / dt, "unit": UNIT, "envs": len(envs), "steps": steps,
+            "launches": steps * len(envs)}
+
+
+def side_workload(name, sc, steps, tune_steps, plain_envs, stream, flush, reps=3):
+    """Batched (autotuned, best of `reps` rollouts by CUDA events) and plain
+    forms of one more workload of the benchmark table."""
+    import torch
+
+    from paper_2505_00690_gb300 import crowd as cw
+
+    with torch.cuda.stream(stream):
+        cr = cw.Crowd(sc, flags=0, stream=stream.cuda_stream)
+        init = torch.from_numpy(sc.state()).cuda()
+        rv = None if sc.robot_vel is None else torch.from_numpy(np.ascontiguousarray(sc.robot_vel[:steps])).cuda()
+    tuning = cr.autotune(n_steps=tune_steps) if tune_steps else cr.tuning()
+    ms, _, _ = time_rollouts(cr, rv, init, steps, reps, 1, stream, flush)
+    cr.close()
+    best = min(ms)
+    value = sc.n_agents * steps / (best / 1e3)
+    plain = plain_form(sc, min(steps, 20), plain_envs, stream)
+    return {"workload": name, "envs": sc.n_envs, "agents": sc.n_agents, "rollout_steps": steps,
+            "value": value, "unit": UNIT, "ms_per_rollout": best, "ms_all": ms, "tuning": tuning,
+            "plain": plain, "batched_over_plain": value / plain["value"]}
 
 
 def run_ours(args):
@@ -146,68 +232,33 @@ def run_ours(args):
     from paper_2505_00690_gb300 import build as B
 
     B.build()
-    sc = scenes.urban_block(seed=replicas.replica_seed(rank), steps=ROLLOUT)
+    sc = scenes.dense_crowd(seed=replicas.replica_seed(rank), steps=ROLLOUT)
     n_agents = sc.n_agents
     with torch.cuda.stream(stream):
         cr = cw.Crowd(sc, flags=0, stream=stream.cuda_stream)
         init = torch.from_numpy(sc.state()).to(dev)
-        rv_dev = torch.from_numpy(np.ascontiguousarray(sc.robot_vel[:ROLLOUT])).to(dev)
         flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
     torch.cuda.synchronize(dev)
+    tuning = cr.autotune(n_steps=ROLLOUT)  # resident shapes only; the dense crowd runs on the tiled path
 
-    # launch shape chosen by the library's autotuner (untimed), each candidate
-    # timed on a whole rollout: the crowded regions that set the rollout time
-    # form over hundreds of steps
-    tuning = cr.autotune(n_steps=ROLLOUT)
-
-    def one_rollout():
-        cr.step(rv_dev, n_steps=ROLLOUT)
-
-    def reset():
-        cr.set_state(init)
-        with torch.cuda.stream(stream):
-            flush.fill_(1.0)
-
-    for _ in range(args.warmup):
-        reset()
-        one_rollout()
-    torch.cuda.synchronize(dev)
-
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    if dist:
-        tdist.barrier()
-    torch.cuda.synchronize(dev)
     with Clocks(local) as clk:
-        t0 = time.perf_counter()
-        for k in range(args.steps):
-            reset()
-            starts[k].record(stream)
-            one_rollout()
-            ends[k].record(stream)
-        torch.cuda.synchronize(dev)
-        wall = time.perf_counter() - t0
-    if dist:
-        tdist.barrier()
-    per = [s.elapsed_time(e) for s, e in zip(starts, ends)]  # ms
-    my_ms = float(sum(per))
+        per, wall, launches = time_rollouts(cr, None, init, ROLLOUT, args.steps, args.warmup, stream, flush, dist)
     clocks = clk.summary()
-    # replicas: this rank's agent-steps, the slowest rank's time
+    my_ms = float(sum(per))
     my_agent_steps = n_agents * ROLLOUT * args.steps
     value = replicas.aggregate_throughput(my_agent_steps, my_ms / 1e3, device=dev)
     total_agent_steps = replicas.sum_over_ranks(my_agent_steps, device=dev)
     dev_ms = replicas.max_over_ranks(my_ms, device=dev)
 
-    # ---- e2e: same rollouts through the C ABI with pinned host buffers
+    # ---- e2e: the same rollouts through the C ABI with pinned host buffers
     init_h = torch.from_numpy(sc.state()).pin_memory()
-    rv_h = torch.from_numpy(np.ascontiguousarray(sc.robot_vel[:ROLLOUT])).pin_memory()
     out_h = torch.empty((n_agents, 4), dtype=torch.float32).pin_memory()
     lib = cw.load()
     import ctypes as C
 
     def e2e_step():
         cw._check(lib.crowd_set_state(cr.h, C.c_void_p(init_h.data_ptr()), cw.CROWD_HOST))
-        cw._check(lib.crowd_step(cr.h, C.c_float(sc.dt), C.c_void_p(rv_h.data_ptr()), cw.CROWD_HOST, ROLLOUT))
+        cw._check(lib.crowd_step(cr.h, C.c_float(sc.dt), None, cw.CROWD_HOST, ROLLOUT))
         cw._check(lib.crowd_read_state(cr.h, C.c_void_p(out_h.data_ptr()), cw.CROWD_HOST))
 
     e2e_step()
@@ -220,55 +271,42 @@ def run_ours(args):
     torch.cuda.synchronize(dev)
     e2e_s = replicas.max_over_ranks(time.perf_counter() - t0, device=dev)
     e2e = {"value": total_agent_steps / e2e_s, "unit": UNIT,
-           "h2d_bytes_per_step": int(init_h.numel() * 4 + rv_h.numel() * 4),
-           "d2h_bytes_per_step": int(out_h.numel() * 4)}
+           "h2d_bytes_per_step": int(init_h.numel() * 4), "d2h_bytes_per_step": int(out_h.numel() * 4)}
 
-    # ---- roofline of the resident kernel (FP32 issue): counted work of one rollout
+    # ---- roofline of the update kernel (FP32 issue): counted work of one rollout
     counted = cw.Crowd(sc, flags=cw.CROWD_FLAG_COUNT_WORK, stream=stream.cuda_stream)
-    counted.step(rv_dev, n_steps=ROLLOUT)
+    counted.step(None, n_steps=ROLLOUT)
     work = counted.work()
     counted.close()
     flops = algorithmic_flops(work)
-    launch_s = dev_ms / 1e3 / args.steps
-    peaks = measured_peaks()
+    step_s = dev_ms / 1e3 / args.steps / ROLLOUT
     sm_mhz = 2070.0
     fp32_peak = N_SMS * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12  # TFLOP/s
-    achieved = flops / launch_s / 1e12
+    achieved = flops / ROLLOUT / step_s / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
-                "frac": achieved / fp32_peak, "traffic": ROLLOUT_DRAM_BYTES,
-                "traffic_last_capture": ROLLOUT_DRAM_BYTES_LAST_CAPTURE,
+                "frac": achieved / fp32_peak,
+                "traffic": UPDATE_DRAM_BYTES,
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz max SM clock",
-                "flops_per_launch": flops, "work_per_agent_step": {k: v / max(1, work["agent_steps"])
-                                                                   for k, v in work.items() if k != "agent_steps"}}
+                "launch": "one step of all 16 environments (the update kernel and its sort kernels, timed together)",
+                "flops_per_launch": flops / ROLLOUT,
+                "work_per_agent_step": {k: v / max(1, work["agent_steps"])
+                                        for k, v in work.items() if k != "agent_steps"}}
 
-    # ---- plain form: one environment per launch, one step per launch, same kernel
-    plain = None
+    extra = {}
     if rank == 0 and not args.no_plain:
-        plain_steps = 20
-        handles = [cw.Crowd(sc.subset([e]), flags=0, stream=stream.cuda_stream) for e in range(sc.n_envs)]
-        rv1 = [torch.from_numpy(np.ascontiguousarray(sc.robot_vel[:plain_steps, e:e + 1])).to(dev)
-               for e in range(sc.n_envs)]
-        for e, h in enumerate(handles):  # warm
-            h.step(rv1[e][:1], n_steps=1)
-        torch.cuda.synchronize(dev)
-        t0 = time.perf_counter()
-        for k in range(plain_steps):
-            for e, h in enumerate(handles):
-                h.step(rv1[e][k:k + 1], n_steps=1)
-        torch.cuda.synchronize(dev)
-        pt = time.perf_counter() - t0
-        plain_value = n_agents * plain_steps / pt
-        plain = {"value": plain_value, "unit": UNIT, "steps": plain_steps,
-                 "launches": plain_steps * sc.n_envs, "batched_over_plain": value / ws / plain_value}
-        for h in handles:
-            h.close()
-
+        p = plain_form(sc, 20, sc.n_envs, stream)
+        p["batched_over_plain"] = value / ws / p["value"]
+        extra["plain"] = p
+    if rank == 0 and not args.no_side:
+        extra["urban_block"] = side_workload("urban_block: 256 envs x (128 peds + 1 robot), 40x40 m, 36 segments/env",
+                                             scenes.urban_block(0), 1000, 1000, 64, stream, flush)
+        extra["uneven_batch"] = side_workload("uneven_batch: 1024 envs, 16-512 agents, 0-40 polygons",
+                                              scenes.uneven_batch(0), 50, 50, 64, stream, flush)
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
         cpu = cpu_baseline(sc, budget_s=args.cpu_seconds)
-
     serving = None
-    if rank == 0 and args.serve:
+    if rank == 0 and not args.no_serve:
         serving = serve_workload(args.serve_seconds)
 
     cr.close()
@@ -277,12 +315,12 @@ def run_ours(args):
                 "warmup": args.warmup, "ms_per_step": dev_ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": {"workload": WORKLOAD, "envs": sc.n_envs, "agents": n_agents, "rollout_steps": ROLLOUT,
-                           "step": "one 1000-step rollout of all envs (crowd_step n_steps=1000)",
+                           "step": f"one {ROLLOUT}-step rollout of all envs (crowd_step n_steps={ROLLOUT})",
                            "l2": "256 MiB buffer written between timed rollouts",
                            "parallelism": f"env replicas x{ws}"},
-                "wall_s": wall, "clocks": clocks, "e2e": e2e, "gpu_launches": args.steps, "tuning": tuning,
-                "roofline": roofline, "cpu_baseline": cpu, "plain": plain, "serving": serving,
-                "kernel_ms": per}
+                "wall_s": wall, "clocks": clocks, "e2e": e2e, "gpu_launches": launches,
+                "tuning": tuning, "roofline": roofline, "cpu_baseline": cpu, "serving": serving,
+                "kernel_ms": per, **extra}
         print(json.dumps(line))
     if dist:
         tdist.destroy_process_group()
@@ -292,42 +330,62 @@ def serve_workload(duration_s):
     """Serving workload: Poisson arrivals at 200 requests/s for duration_s,
     one environment each (32..2048 agents log-uniform, 0..60 convex polygons,
     100..1000 steps), through the continuous-batching server (4 GiB budget,
-    1024 slots, 50 steps per tick); plus the plain form (one request at a
-    time, one step per launch) on the first 20 requests."""
+    1024 slots, 50 steps per tick); the plain form (one request at a time,
+    one step per launch) on the first 20 requests; and a sweep of arrival
+    rates over the same requests, their arrival times scaled by 200/rate
+    (a Poisson stream at that rate), so that the sustainable throughput and
+    the latency knee show."""
     from paper_2505_00690_gb300 import crowd as cw
     from paper_2505_00690_gb300 import scenes
     from paper_2505_00690_gb300 import serve
 
-    reqs = scenes.serving_stream(seed=0, rate=200.0, duration_s=duration_s)
+    reqs = scenes.serving_stream(seed=0, rate=SERVE_RATES[0], duration_s=duration_s)
     sc0 = reqs[0].scene
     params = cw.params_for(sc0)
     out = serve.run_stream(reqs, params, sc0.dt, chunk_steps=50, max_slots=1024, mem_budget=4 << 30)
     out.pop("results", None)
-    plain = serve.run_plain(reqs[:20], params, sc0.dt)
-    out["plain_agent_steps_per_s"] = plain
-    out["rate_req_per_s"] = 200.0
+    out["rate_req_per_s"] = SERVE_RATES[0]
+    out["plain_agent_steps_per_s"] = serve.run_plain(reqs[:20], params, sc0.dt)
+    sweep = []
+    for rate in SERVE_RATES:
+        scaled = [scenes.Request(arrival_s=r.arrival_s * SERVE_RATES[0] / rate, scene=r.scene, steps=r.steps)
+                  for r in reqs]
+        s = serve.run_stream(scaled, params, sc0.dt, chunk_steps=50, max_slots=1024, mem_budget=4 << 30)
+        sweep.append({"rate_req_per_s": rate, "p50_s": s["p50_s"], "p99_s": s["p99_s"],
+                      "agent_steps_per_s": s["agent_steps_per_s"], "requests": s["requests"],
+                      "max_live": s["max_live"], "wall_s": s["wall_s"]})
+    out["sweep"] = sweep
     return out
 
 
 def cpu_baseline(sc, budget_s=12.0, threads=None):
-    """The FP64 oracle as it stands, on the host cores, on a bounded sample:
-    consecutive steps of the full 256-env batch until about budget_s."""
+    """The FP64 oracle as it stands, on the host cores, on a bounded sample of
+    the headline workload: consecutive steps of environment 0 (20,000
+    agents, all of them) from the initial state until about budget_s; beside
+    it the 1000-agent subset the teacher-forced parity test uses."""
     import oracle
 
     threads = threads or os.cpu_count() or 1
-    o = oracle.OracleScene(sc)
-    pos = sc.pos.astype(np.float64)
-    vel = sc.vel.astype(np.float64)
+    one = sc.subset([0])
+    o = oracle.OracleScene(one)
+    pos = one.pos.astype(np.float64)
+    vel = one.vel.astype(np.float64)
     steps = 0
     t0 = time.perf_counter()
     while True:
-        pos, vel, _, _ = o.step(pos, vel, sc.robot_vel_at(steps), threads=threads)
+        pos, vel, _, _ = o.step(pos, vel, None, threads=threads)
         steps += 1
         if time.perf_counter() - t0 >= budget_s or steps >= ROLLOUT:
             break
     dt = time.perf_counter() - t0
-    return {"value": sc.n_agents * steps / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": f"{steps} consecutive steps of all {sc.n_envs} envs ({sc.n_agents} agents), FP64, OpenMP over agents"}
+    sel = np.random.default_rng(0).choice(one.n_agents, 1000, replace=False)
+    t1 = time.perf_counter()
+    o.step(one.pos.astype(np.float64), one.vel.astype(np.float64), None, sel=sel, threads=threads)
+    sub_dt = time.perf_counter() - t1
+    return {"value": one.n_agents * steps / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"{steps} consecutive steps of env 0 ({one.n_agents} agents) from the initial state, FP64, "
+                      f"OpenMP over agents",
+            "subset_1000_agents": {"value": 1000 / sub_dt, "unit": UNIT, "steps": 1}}
 
 
 def cpu_table(budget_s=6.0):
@@ -364,38 +422,35 @@ def cpu_table(budget_s=6.0):
 
 
 def run_reference(args):
+    """The reference arm: the FP64 oracle as it stands on the host cores.  Each
+    benchmark step is a bounded sample of the headline workload: one ORCA
+    step of all 16 environments (320,000 agents) from the initial state on."""
     ws, rank, local = _dist_env()
     if rank != 0:
         return
     from paper_2505_00690_gb300 import scenes
 
-    sc = scenes.urban_block(seed=0, steps=ROLLOUT)
+    sc = scenes.dense_crowd(seed=0, steps=ROLLOUT)
     import oracle
 
     threads = os.cpu_count() or 1
     o = oracle.OracleScene(sc)
     pos = sc.pos.astype(np.float64)
     vel = sc.vel.astype(np.float64)
-    sample_steps = 2  # each benchmark step: 2 ORCA steps of the full batch
-    k = 0
     for _ in range(args.warmup):
-        for _ in range(sample_steps):
-            pos, vel, _, _ = o.step(pos, vel, sc.robot_vel_at(k), threads=threads)
-            k += 1
+        pos, vel, _, _ = o.step(pos, vel, None, threads=threads)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        for _ in range(sample_steps):
-            pos, vel, _, _ = o.step(pos, vel, sc.robot_vel_at(k), threads=threads)
-            k += 1
+        pos, vel, _, _ = o.step(pos, vel, None, threads=threads)
     dt = time.perf_counter() - t0
-    value = sc.n_agents * sample_steps * args.steps / dt
+    value = sc.n_agents * args.steps / dt
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
             "config": {"workload": WORKLOAD, "envs": sc.n_envs, "agents": sc.n_agents,
-                       "step": f"{sample_steps} ORCA steps of all envs (bounded sample of the 1000-step rollout)"},
+                       "step": "one ORCA step of all envs (bounded sample of the 500-step rollout)"},
             "cpu_baseline": {"value": value, "unit": UNIT, "kind": "oracle", "cores": threads,
-                             "sample": f"{sample_steps} steps x {args.steps} timed of all {sc.n_envs} envs"},
+                             "sample": f"1 step x {args.steps} timed of all {sc.n_envs} envs ({sc.n_agents} agents)"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
@@ -405,7 +460,8 @@ def profile_case(which):
     256-env urban block (after one warm launch); `rollout` = the same with the
     full 1000-step rollout (for one-pass counters only); `tiled` = two single
     steps of one 20,000-agent dense-crowd environment (the second is
-    captured)."""
+    captured); `dense` = two single steps of the 16-environment dense crowd
+    (the headline workload; the second step's update is captured)."""
     from paper_2505_00690_gb300 import build as B
     from paper_2505_00690_gb300 import crowd as cw
     from paper_2505_00690_gb300 import scenes
@@ -418,13 +474,16 @@ def profile_case(which):
         cr.set_state(sc.state())
         cr.step(sc.robot_vel[:20], n_steps=20)
     elif which == "rollout":
-        # the timed launch of the default run: one 1000-step rollout of the
-        # 256-env urban block (default launch shape), after a warm one
-        sc = scenes.urban_block(0, steps=ROLLOUT)
+        sc = scenes.urban_block(0, steps=1000)
         cr = cw.Crowd(sc)
-        cr.step(sc.robot_vel[:ROLLOUT], n_steps=ROLLOUT)
+        cr.step(sc.robot_vel[:1000], n_steps=1000)
         cr.set_state(sc.state())
-        cr.step(sc.robot_vel[:ROLLOUT], n_steps=ROLLOUT)
+        cr.step(sc.robot_vel[:1000], n_steps=1000)
+    elif which == "dense":
+        sc = scenes.dense_crowd(0, steps=4)
+        cr = cw.Crowd(sc)
+        cr.step(n_steps=1)
+        cr.step(n_steps=1)
     else:
         sc = scenes.dense_crowd(0, n_envs=1, steps=4)
         cr = cw.Crowd(sc)
@@ -435,6 +494,31 @@ def profile_case(which):
     print(json.dumps({"profile_case": which, "agents": sc.n_agents}))
 
 
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def launch_replicas(args):
+    """`--gpus N` outside a launcher: one replica process per GPU through
+    torch.distributed.run (the same launch the contract uses), or an error
+    when fewer than N GPUs are visible.  Returns the exit code."""
+    try:
+        import torch
+
+        visible = torch.cuda.device_count()
+    except Exception:
+        visible = 0
+    if visible < args.gpus:
+        print(f"bench.py: --gpus {args.gpus} requested but {visible} GPU(s) visible", file=sys.stderr)
+        return 2
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", f"--nproc-per-node={args.gpus}",
+           "--master-addr", "127.0.0.1", "--master-port", str(_free_port()), os.path.abspath(__file__)]
+    cmd += [a for a in sys.argv[1:]]
+    return subprocess.call(cmd)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -442,25 +526,38 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-side", action="store_true", help="leave out the urban-block and uneven-batch keys")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-serve", action="store_true", help="leave out the serving replay and its rate sweep")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
-    ap.add_argument("--serve", action="store_true",
-                    help="also replay the serving workload (Poisson request stream) and report p50/p99 latency")
     ap.add_argument("--serve-seconds", type=float, default=10.0)
     ap.add_argument("--cpu-table", action="store_true",
                     help="time the FP64 oracle on every workload (1 and all host threads) and exit")
-    ap.add_argument("--profile-case", choices=["resident", "rollout", "tiled"], default=None,
+    ap.add_argument("--profile-case", choices=["resident", "rollout", "tiled", "dense"], default=None,
                     help="run a small case for an ncu capture and exit")
     args = ap.parse_args()
     if args.cpu_table:
         cpu_table()
-    elif args.profile_case:
+        return 0
+    if args.profile_case:
         profile_case(args.profile_case)
-    elif args.impl == "reference":
+        return 0
+    ws, rank, _ = _dist_env()
+    launched = "LOCAL_RANK" in os.environ and "WORLD_SIZE" in os.environ
+    if args.gpus < 1:
+        print("bench.py: --gpus must be >= 1", file=sys.stderr)
+        return 2
+    if launched and ws != args.gpus:
+        print(f"bench.py: --gpus {args.gpus} differs from the launcher's WORLD_SIZE {ws}", file=sys.stderr)
+        return 2
+    if not launched and args.gpus > 1:
+        return launch_replicas(args)
+    if args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)
+    return 0
 
 
 if __name__ == "__main__":
-    main()
+    sys.exit(main())

@@ -127,6 +127,11 @@ typedef struct {
 } crowd_env_stats;
 
 /* Create a batch of n_envs environments on the current CUDA device.
+ * Paper: Sec. 3.2 -- the dynamic agents of many parallel environments, each
+ * with its radius and maximum speed, the ORCA time horizon and neighbour
+ * distance, the static objects of the generated scene (segments) and the
+ * trained robot as one more agent; Sec. 3.3 -- environments of different
+ * sizes side by side in one batch.
  *   agents_per_env [n_envs]     agents of each environment (>= 0)
  *   radii, max_speeds [N]       r > 0, v_max >= 0 (N = total agents)
  *   pref_speeds [N] or NULL     preferred walking speed; NULL means v_max
@@ -142,7 +147,9 @@ crowd_status crowd_create(int32_t n_envs, const int32_t* agents_per_env, const f
                           const int32_t* robot_index, const int32_t* segs_per_env, const float* segments,
                           const crowd_params* p, void* cuda_stream, crowd_t* out);
 
-/* Goals [N][2] (fixed goals; removes a goal queue). */
+/* Goals [N][2] (fixed goals; removes a goal queue).
+ * Paper: Sec. 3.2 -- every agent gets a sampled end point and walks toward
+ * it (the preferred velocity of step A0). */
 crowd_status crowd_set_goals(crowd_t h, const float* goals, int32_t ptr_kind);
 
 /* Goal queues (continuing walks after arrival; the paper's agents walk
@@ -178,12 +185,14 @@ crowd_status crowd_set_goal_queue(crowd_t h, int32_t n_goals, const float* goals
 crowd_status crowd_set_goal_pool(crowd_t h, const int32_t* pool_start, const float* points, uint64_t seed);
 
 /* Host copy [N] of how many goals each agent has moved past (queue) or drawn
- * (pool) since they were set (0 without either).  Waits. */
+ * (pool) since they were set (0 without either).  Waits.
+ * Paper: Sec. 3.2 (end points sampled per agent); the counter is this
+ * library's read-back of the goal queues and pools above. */
 crowd_status crowd_read_goal_index(crowd_t h, int32_t* out);
 
 /* Lane-following vehicles (the paper's city scenes run cars beside the
  * crowd under the Intelligent Driver Model of Treiber, Hennecke and Helbing,
- * 2000).  Lanes are closed polylines: lane l has points
+ * 2000; Appendix "Data", and Sec. 3.2's vehicles among the dynamic agents).  Lanes are closed polylines: lane l has points
  * points[lane_start[l]..lane_start[l+1]) ([P][2], at least 2, no zero-length
  * segment; the last point joins the first).  Vehicle k (agents ascending) is
  * crowd agent `agent[k]` (global index, not a robot slot, at most
@@ -208,7 +217,9 @@ crowd_status crowd_set_vehicles(crowd_t h, int32_t n_lanes, const int32_t* lane_
                                 const float* v, const float* params, float half_width, float lookahead);
 
 /* Arc positions s [V] and speeds v [V] of the vehicles: written from the host
- * when `write` != 0 (s in [0, lane length), v >= 0), else read.  Waits. */
+ * when `write` != 0 (s in [0, lane length), v >= 0), else read.  Waits.
+ * Paper: Appendix "Data" (cars under the IDM beside the crowd); reading and
+ * writing their state is this library's checkpoint of them. */
 crowd_status crowd_vehicle_state(crowd_t h, int32_t write, float* s, float* v);
 
 /* Episodes: environments start over inside multi-step calls, each on its own
@@ -231,7 +242,8 @@ crowd_status crowd_vehicle_state(crowd_t h, int32_t write, float* s, float* v);
  * in a host init_state.  Copies; waits for the stream. */
 crowd_status crowd_set_episodes(crowd_t h, const int32_t* steps, const float* init_state, int32_t ptr_kind);
 
-/* Per-environment reset mask: the environments with mask[e] != 0 start over
+/* Paper: Sec. 3.3 (episodes that differ per environment).
+ * Per-environment reset mask: the environments with mask[e] != 0 start over
  * now, between calls, from the snapshot of crowd_set_episodes (agent rows,
  * goals, goal-queue counters, car arcs), as a scheduled start does; the
  * others keep their state.  For episodes that end on events (a collision, an
@@ -240,29 +252,48 @@ crowd_status crowd_set_episodes(crowd_t h, const int32_t* steps, const float* in
 crowd_status crowd_restart_envs(crowd_t h, const uint8_t* mask);
 
 /* Full state [N][4] (px, py, vx, vy): resume from a checkpoint, or teacher
- * forcing from another simulator's state. */
+ * forcing from another simulator's state.
+ * Paper: Sec. 3.2 -- the agents' positions and velocities, the state the
+ * per-step adjustment reads. */
 crowd_status crowd_set_state(crowd_t h, const float* state, int32_t ptr_kind);
 
 /* Advance every environment by n_steps >= 1 steps of length dt > 0.
+ * Paper: Sec. 3.2 -- every step each agent's velocity is adjusted in real
+ * time from the proximity and relative velocity of the others (ORCA, steps
+ * A0-A6 above), reacting to the trained robot, whose velocity is the action
+ * given here; Sec. 3.3 -- all environments are stepped together on the GPU.
  * robot_vel [n_steps][n_envs][2] m/s, the robot command of each step
  * (entries of environments without a robot are ignored); NULL keeps every
  * robot at its current velocity. */
 crowd_status crowd_step(crowd_t h, float dt, const float* robot_vel, int32_t ptr_kind, int32_t n_steps);
 
-/* Copy the state [N][4] (px, py, vx, vy) out; waits for the stream. */
+/* Copy the state [N][4] (px, py, vx, vy) out; waits for the stream.
+ * Paper: Sec. 3.2 -- the adjusted agent positions (and velocities) that the
+ * simulator hands to the rest of the platform each step. */
 crowd_status crowd_read_state(crowd_t h, float* out, int32_t ptr_kind);
 
 /* Neighbour lists [N][K] of the last step (environment-local indices, -1
- * padded), only with CROWD_FLAG_EXPORT_NEIGHBORS; waits for the stream. */
+ * padded), only with CROWD_FLAG_EXPORT_NEIGHBORS; waits for the stream.
+ * Paper: Sec. 3.2 ("proximity": the agents each one reacts to, step A2). */
 crowd_status crowd_read_neighbors(crowd_t h, int32_t* out, int32_t ptr_kind);
 
 /* Host copies of the per-environment statistics [n_envs] and of the goal
  * reach step of every agent [N] (1-based global step index after which
- * |g - p| <= r first held, -1 if not yet); either may be NULL.  Waits. */
+ * |g - p| <= r first held, -1 if not yet); either may be NULL.  Waits.
+ * Paper: Appendix "Evaluation Metrics" (collision indicator, speed, goal
+ * reached). */
 crowd_status crowd_read_stats(crowd_t h, crowd_env_stats* env_stats, int32_t* reach_step);
 
-/* Host copy of the work counters (only with CROWD_FLAG_COUNT_WORK). */
+/* Host copy of the work counters (only with CROWD_FLAG_COUNT_WORK).
+ * No counterpart in the paper: the units of the step's algorithmic
+ * operation count (Sec. 3.2's step, counted for the roofline). */
 crowd_status crowd_read_work(crowd_t h, crowd_work* out);
+
+/* Kernels this handle's crowd_step calls have enqueued since it was created
+ * (a replayed CUDA graph counts its kernels), into *out; host-side count, no
+ * wait.  No counterpart in the paper: it lets a caller count the library's
+ * launches inside a timed region. */
+crowd_status crowd_read_launches(crowd_t h, int64_t* out);
 
 /* Launch shape of the shared-memory-resident kernel (environments of up to
  * 2048 agents).  None of these changes results except coop_fallback, which
@@ -294,10 +325,13 @@ typedef struct {
     int32_t agent_order;
 } crowd_tuning;
 
+/* Read / set the launch shape.  No counterpart in the paper (this
+ * library's launch parameters for Sec. 3.2's step). */
 crowd_status crowd_get_tuning(crowd_t h, crowd_tuning* out);
 crowd_status crowd_set_tuning(crowd_t h, const crowd_tuning* t);
 
-/* Time every tuning candidate (one lane per agent: block_threads
+/* No counterpart in the paper (chooses this library's launch shape).
+ * Time every tuning candidate (one lane per agent: block_threads
  * default/64/128/256/512 x coop_fallback 0 and 2 x cell_split 1-3 x
  * agent_order; 2, 4 and 8 lanes per agent: the default block and 512 threads
  * x cell_split 1-2) over n_steps steps of length dt from the current state, keep
@@ -305,16 +339,20 @@ crowd_status crowd_set_tuning(crowd_t h, const crowd_tuning* t);
  * stream; allocates temporary device memory.  `chosen` may be NULL. */
 crowd_status crowd_autotune(crowd_t h, float dt, int32_t n_steps, crowd_tuning* chosen);
 
-/* Zero the statistics and reach steps and restart the step counter at 0. */
+/* Zero the statistics and reach steps and restart the step counter at 0.
+ * Paper: Appendix "Evaluation Metrics" (the statistics reset here). */
 crowd_status crowd_reset_stats(crowd_t h);
 
-/* Wait for all work enqueued on the handle; reports a device error word. */
+/* Wait for all work enqueued on the handle; reports a device error word.
+ * No counterpart in the paper (stream ordering of this library). */
 crowd_status crowd_synchronize(crowd_t h);
 
-/* Release the handle and its device memory (waits for the stream first). */
+/* Release the handle and its device memory (waits for the stream first).
+ * No counterpart in the paper (resource lifetime of this library). */
 crowd_status crowd_destroy(crowd_t h);
 
-/* Number of agents / environments of a handle (0 for NULL). */
+/* Number of agents / environments of a handle (0 for NULL).
+ * Paper: Sec. 3.2-3.3 (agents per environment, parallel environments). */
 int64_t crowd_num_agents(crowd_t h);
 int32_t crowd_num_envs(crowd_t h);
 
@@ -360,23 +398,31 @@ typedef struct {
     size_t bytes_in_use;
 } crowd_server_stats;
 
-/* Create a server on the current device (allocates its slot arena; all
+/* Serving: Sec. 3.3's many non-uniform environments, here as rollout
+ * requests of different sizes admitted while others run.
+ * Create a server on the current device (allocates its slot arena; all
  * pointers host).  dt is the step length of every request. */
 crowd_status crowd_server_create(const crowd_params* p, float dt, const crowd_server_config* cfg, void* cuda_stream,
                                  crowd_server_t* out);
-/* Validate and copy a request (host pointers); its id is written to *id. */
+/* Validate and copy a request (host pointers); its id is written to *id.
+ * Paper: Sec. 3.3 (one more non-uniform environment joins the batch). */
 crowd_status crowd_server_submit(crowd_server_t s, const crowd_request* r, int64_t* id);
 /* Retire the previous tick (waits for it), admit, and enqueue the next chunk.
+ * Paper: Sec. 3.2-3.3 (all live environments stepped together on the GPU).
  * n_live: requests stepped by this tick; n_finished: requests the previous
  * tick completed.  Either may be NULL. */
 crowd_status crowd_server_tick(crowd_server_t s, int32_t* n_live, int32_t* n_finished);
-/* Status of a request (CROWD_REQ_*); when done, its final state [n][4] is
+/* Paper: Sec. 3.2 (the adjusted agent states of a finished request).
+ * Status of a request (CROWD_REQ_*); when done, its final state [n][4] is
  * copied to out_state (if not NULL) and the request is forgotten. */
 crowd_status crowd_server_poll(crowd_server_t s, int64_t id, float* out_state, int32_t* status);
-/* Ids of up to `cap` requests completed since the last call (oldest first);
+/* No counterpart in the paper (completion queue of the serving loop).
+ * Ids of up to `cap` requests completed since the last call (oldest first);
  * *n receives how many were written.  Their results stay available to
  * crowd_server_poll. */
 crowd_status crowd_server_finished(crowd_server_t s, int64_t* ids, int32_t cap, int32_t* n);
+/* Waiting / live requests and bytes in use; release the server.
+ * No counterpart in the paper (admission state and lifetime of this library). */
 crowd_status crowd_server_info(crowd_server_t s, crowd_server_stats* out);
 crowd_status crowd_server_destroy(crowd_server_t s);
 
@@ -400,14 +446,18 @@ crowd_status crowd_server_destroy(crowd_server_t s);
  *     (other streams, other host threads) race on it -- serialise them.
  *   - The first call on a device looks up the array's address with that
  *     device current and sets a kernel attribute; make it before any stream
- *     capture.  Each call waits once for the stream (to check the size of the
- *     segment lists).
+ *     capture.  Each call waits for the stream twice: to check the size of
+ *     the segment lists, and at the end to read the device error word (an
+ *     agent with more than CROWD_MAX_OBSTACLE_LINES segments in reach keeps
+ *     the nearest ones and the call returns CROWD_EDEVICE, as crowd_step's
+ *     next synchronising call would).
  *   - Device pointers: state_in [n][4] (px, py, vx, vy; the robot slot moves
  *     with the velocity stored there), state_out [n][4] (must not alias
  *     state_in), agent_params [n][4] (r, v_max, preferred speed, unused),
  *     goals [n][2], segments [n_segments][4] (zero-length segments are
  *     ignored).  Host pointers: box [4] (x0, y0, x1, y1), the region the grid
- *     covers (agents outside it are still handled exactly), and p.
+ *     covers, and p.  The box must contain every segment (CROWD_EINVAL
+ *     otherwise); agents may leave it and are still handled exactly.
  *   - Results match crowd_step on a handle holding the same environment. */
 #define CROWD_NOALLOC_MAX_AGENTS 65536
 #define CROWD_NOALLOC_MAX_CELLS 65536
@@ -440,7 +490,9 @@ crowd_status crowd_map_segments(const uint8_t* occ, int32_t W, int32_t H, float 
                                 int32_t closed, int32_t max_segments, float* segments, int32_t* n_segments,
                                 void* stream);
 
-/* crowd_map_sample: n_points points [n][2] into DEVICE `points`, uniform over
+/* Paper: Sec. 3.2 (random start and end points on the traversable area of
+ * the occupancy map).
+ * crowd_map_sample: n_points points [n][2] into DEVICE `points`, uniform over
  * the cells that are free and have no obstacle (and, when closed, no outside)
  * within `clearance` cells in x and y (0..CROWD_MAP_MAX_CLEARANCE).  Point k
  * draws (u0, u1, u2, u3) = Philox4x32-10(counter (k, stream_id, 0, 0), key
@@ -453,11 +505,13 @@ crowd_status crowd_map_sample(const uint8_t* occ, int32_t W, int32_t H, float ce
                               int32_t closed, int32_t clearance, uint64_t seed, uint32_t stream_id, int32_t n_points,
                               float* points, int32_t* n_eligible, void* stream);
 
-/* Message for the calling thread's last failed call ("" if none). */
+/* Message for the calling thread's last failed call ("" if none).
+ * No counterpart in the paper (error reporting of this C interface). */
 const char* crowd_last_error(void);
 
-/* Library ABI version (increments on any signature change). */
-int32_t crowd_abi_version(void);  /* 3: adds crowd_set_episodes, crowd_restart_envs, crowd_set_goal_pool */
+/* Library ABI version (increments on any signature change).
+ * No counterpart in the paper. */
+int32_t crowd_abi_version(void);  /* 4: adds crowd_read_launches */
 
 #ifdef __cplusplus
 }

@@ -31,7 +31,7 @@ EXPORTED = ["crowd_create", "crowd_set_goals", "crowd_set_state", "crowd_step", 
             "crowd_destroy", "crowd_num_agents", "crowd_num_envs", "crowd_last_error", "crowd_abi_version",
             "crowd_get_tuning", "crowd_set_tuning", "crowd_autotune", "crowd_set_goal_queue",
             "crowd_read_goal_index", "crowd_set_vehicles", "crowd_vehicle_state", "crowd_set_episodes",
-            "crowd_restart_envs", "crowd_set_goal_pool"]
+            "crowd_restart_envs", "crowd_set_goal_pool", "crowd_read_launches"]
 
 
 class CrowdError(RuntimeError):
@@ -88,6 +88,7 @@ def load(path: str = LIB_PATH):
     L.crowd_read_neighbors.argtypes = [vp, vp, i32]
     L.crowd_read_stats.argtypes = [vp, vp, vp]
     L.crowd_read_work.argtypes = [vp, vp]
+    L.crowd_read_launches.argtypes = [vp, vp]
     L.crowd_reset_stats.argtypes = [vp]
     L.crowd_get_tuning.argtypes = [vp, vp]
     L.crowd_set_tuning.argtypes = [vp, vp]
@@ -203,6 +204,12 @@ def crowd_read_work(h):
     w = crowd_work()
     _check(load().crowd_read_work(h, C.byref(w)))
     return {n: int(getattr(w, n)) for n, _ in crowd_work._fields_}
+
+
+def crowd_read_launches(h):
+    n = C.c_int64()
+    _check(load().crowd_read_launches(h, C.byref(n)))
+    return int(n.value)
 
 
 def crowd_get_tuning(h):
@@ -346,6 +353,11 @@ class Crowd:
 
     def work(self):
         return crowd_read_work(self.h)
+
+    def launches(self):
+        """Kernels this handle's steps have enqueued so far (graph replays by
+        their kernels)."""
+        return crowd_read_launches(self.h)
 
     def tuning(self):
         return crowd_get_tuning(self.h)

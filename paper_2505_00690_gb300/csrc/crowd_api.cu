@@ -146,6 +146,8 @@ struct crowd_ctx {
     long long* d_step = nullptr;
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t graph = nullptr;
+    int64_t graph_kernels = 0;    // kernel launches one replay of `graph` performs
+    int64_t kernel_launches = 0;  // kernels this handle's steps enqueued (graph replays by their kernels)
     struct GraphKey {
         int n_steps = 0;
         float dt = 0.f;
@@ -523,6 +525,7 @@ crowd_status resident_launch(crowd_t h, float dt, const float2* rv, int n_steps,
         h->broken = e != cudaErrorInvalidValue && e != cudaErrorInvalidConfiguration;
         return cuda_fail(e, "launch crowd step");
     }
+    h->kernel_launches += 1;
     return CROWD_OK;
 }
 
@@ -566,6 +569,7 @@ crowd_status resident_steps(crowd_t h, float dt, const float2* rv, int n_steps, 
             restart_resident_envs<<<dim3(h->n_res, (span + 255) / 256), 256, 0, s>>>(
                 ep, h->order, h->env_start, veh, h->state, h->goal, h->goal_idx, h->step_index + k);
             CUDA_TRY(cudaGetLastError(), "episode start");
+            h->kernel_launches += 1;
         }
         const int next = q < starts.size() ? starts[q] : n_steps;
         crowd_status st = resident_launch(h, dt, rv ? rv + (size_t)k * h->E : nullptr, next - k, h->step_index + k,
@@ -637,9 +641,10 @@ std::vector<int> tiled_stats_before(crowd_t h, int n_steps, bool stats) {
 // two state buffers; an odd count ends with the tiled environments copied
 // back; with statistics a last pass counts the collisions of the final state.
 cudaError_t enqueue_tiled(crowd_t h, float dt, const float2* rv, int n_steps, bool stats, float tau_o,
-                          cudaStream_t s) {
+                          cudaStream_t s, int64_t& kernels) {
     const std::vector<int> before = tiled_stats_before(h, n_steps, stats);
     size_t nb = 0;
+    int nk = 0;
     for (int k = 0; k < n_steps; ++k) {
         const bool apart = nb < before.size() && before[nb] == k;
         if (apart) {
@@ -648,12 +653,14 @@ cudaError_t enqueue_tiled(crowd_t h, float dt, const float2* rv, int n_steps, bo
             // that an episode's last state is counted and its restart not
             ++nb;
             cudaError_t e = launch_tiled_step(tiled_args(h, dt, nullptr, k, n_steps, stats, tau_o, kTiledStatsOnly),
-                                              h->tiled_max_agents, h->tiled_max_tiles, s);
+                                              h->tiled_max_agents, h->tiled_max_tiles, s, &nk);
+            kernels += nk;
             if (e != cudaSuccess) return e;
         }
         const int mode = (stats && k > 0 && !apart) ? kTiledStepCount : kTiledStep;
         cudaError_t e = launch_tiled_step(tiled_args(h, dt, rv, k, n_steps, stats, tau_o, mode), h->tiled_max_agents,
-                                          h->tiled_max_tiles, s);
+                                          h->tiled_max_tiles, s, &nk);
+        kernels += nk;
         if (e != cudaSuccess) return e;
     }
     if (n_steps & 1) {
@@ -666,7 +673,8 @@ cudaError_t enqueue_tiled(crowd_t h, float dt, const float2* rv, int n_steps, bo
     }
     if (stats) {
         cudaError_t e = launch_tiled_step(tiled_args(h, dt, nullptr, 0, 1, stats, tau_o, kTiledStatsOnly),
-                                          h->tiled_max_agents, h->tiled_max_tiles, s);
+                                          h->tiled_max_agents, h->tiled_max_tiles, s, &nk);
+            kernels += nk;
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
@@ -678,8 +686,11 @@ cudaError_t enqueue_tiled(crowd_t h, float dt, const float2* rv, int n_steps, bo
 crowd_status tiled_steps(crowd_t h, float dt, const float2* rv, int n_steps, bool stats, float tau_o) {
     cudaError_t e = launch_set_step(h->d_step, h->step_index, h->stream);
     if (e != cudaSuccess) return cuda_fail(e, "set step index");
+    h->kernel_launches += 1;
     if (n_steps == 1) {
-        e = enqueue_tiled(h, dt, rv, n_steps, stats, tau_o, h->stream);
+        int64_t nk = 0;
+        e = enqueue_tiled(h, dt, rv, n_steps, stats, tau_o, h->stream, nk);
+        h->kernel_launches += nk;
         if (e != cudaSuccess) return cuda_fail(e, "launch tiled step");
         return CROWD_OK;
     }
@@ -696,7 +707,8 @@ crowd_status tiled_steps(crowd_t h, float dt, const float2* rv, int n_steps, boo
         cudaGraph_t g = nullptr;
         e = cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal);
         if (e != cudaSuccess) return cuda_fail(e, "begin graph capture");
-        cudaError_t le = enqueue_tiled(h, dt, rv, n_steps, stats, tau_o, h->cap_stream);
+        int64_t nk = 0;
+        cudaError_t le = enqueue_tiled(h, dt, rv, n_steps, stats, tau_o, h->cap_stream, nk);
         e = cudaStreamEndCapture(h->cap_stream, &g);
         if (le != cudaSuccess) {
             if (g) cudaGraphDestroy(g);
@@ -710,9 +722,11 @@ crowd_status tiled_steps(crowd_t h, float dt, const float2* rv, int n_steps, boo
             return cuda_fail(e, "instantiate graph");
         }
         h->gkey = key;
+        h->graph_kernels = nk;
     }
     e = cudaGraphLaunch(h->graph, h->stream);
     if (e != cudaSuccess) return cuda_fail(e, "launch graph");
+    h->kernel_launches += h->graph_kernels;
     return CROWD_OK;
 }
 
@@ -720,7 +734,7 @@ crowd_status tiled_steps(crowd_t h, float dt, const float2* rv, int n_steps, boo
 
 extern "C" {
 
-int32_t crowd_abi_version(void) { return 3; }  // 3: episodes (crowd_set_episodes, crowd_restart_envs)
+int32_t crowd_abi_version(void) { return 4; }  // 4: crowd_read_launches
 
 const char* crowd_last_error(void) { return g_last_error.c_str(); }
 
@@ -1413,6 +1427,14 @@ crowd_status crowd_read_stats(crowd_t h, crowd_env_stats* env_stats, int32_t* re
             env_stats[e].steps = (int64_t)tmp[e].steps;
         }
     return st;
+}
+
+crowd_status crowd_read_launches(crowd_t h, int64_t* out) {
+    crowd_status st = check_handle(h);
+    if (st) return st;
+    if (!out) return fail(CROWD_EINVAL, "out is null");
+    *out = h->kernel_launches;
+    return CROWD_OK;
 }
 
 crowd_status crowd_read_work(crowd_t h, crowd_work* out) {

@@ -242,7 +242,10 @@ cudaError_t tiled_init(int halo_cap);
 // Enqueue one thread setting the device step counter.
 cudaError_t launch_set_step(long long* p, long long value, cudaStream_t s);
 // Enqueue one step of the tiled path (4 kernels + bookkeeping).
-cudaError_t launch_tiled_step(const TiledStepArgs& a, int max_agents, int max_tiles, cudaStream_t s);
+// Enqueues one tiled step; *n_kernels (if given) receives how many kernels it
+// launched.
+cudaError_t launch_tiled_step(const TiledStepArgs& a, int max_agents, int max_tiles, cudaStream_t s,
+                              int* n_kernels = nullptr);
 
 size_t resident_smem_bytes(int max_agents, int K, int block);
 

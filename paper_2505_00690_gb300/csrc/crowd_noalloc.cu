@@ -63,6 +63,7 @@ struct Misc {
     int err;
     float reach;
     int seg_total;
+    int seg_outside;  // a segment endpoint lies outside the caller's box
 };
 
 std::mutex g_setup_mutex;
@@ -87,13 +88,23 @@ crowd_status scratch_address(unsigned char** out) {
     return CROWD_OK;
 }
 
-// Largest r + tau_o v_max over the agents (one CTA), into misc->reach.
-__global__ void na_reach(const float4* par, int n, float tau_o, Misc* misc) {
+// Largest r + tau_o v_max over the agents (one CTA), into misc->reach; a
+// segment with an endpoint outside the box [x0, x1] x [y0, y1] sets
+// misc->seg_outside (an agent outside the grid is clamped into a border
+// cell, whose segment list is complete for it only when every segment lies
+// inside the grid).
+__global__ void na_reach(const float4* par, int n, float tau_o, const float4* segs, int ns, float x0, float y0,
+                         float x1, float y1, Misc* misc) {
     __shared__ float red[32];
     float m = 0.f;
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
         const float4 q = par[i];
         m = fmaxf(m, q.x + tau_o * q.y);
+    }
+    for (int s = threadIdx.x; s < ns; s += blockDim.x) {
+        const float4 g = segs[s];
+        if (!(fminf(g.x, g.z) >= x0 && fmaxf(g.x, g.z) <= x1 && fminf(g.y, g.w) >= y0 && fmaxf(g.y, g.w) <= y1))
+            misc->seg_outside = 1;
     }
     for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
@@ -106,15 +117,21 @@ __global__ void na_reach(const float4* par, int n, float tau_o, Misc* misc) {
 
 // Segment s is listed in a cell when it comes within reach + half the cell
 // diagonal of the cell's centre (so within reach of every point the cell
-// holds, clamped agents from outside the grid included).
+// holds, clamped agents from outside the grid included).  The test runs in
+// coordinates relative to the grid origin, so that the cell centres carry no
+// rounding error of a large offset; the margin still covers the FP32 error
+// of moving the endpoints there, a few units of 2^-24 of |x0| + |y0| + the
+// grid's extent.
 __device__ __forceinline__ bool seg_near_cell(const TiledEnv& te, float4 sg, int cell, float reach) {
     const float c = 1.f / te.inv_c;
-    const float px = te.x0 + ((cell % te.W) + 0.5f) * c, py = te.y0 + ((cell / te.W) + 0.5f) * c;
-    const float ex = sg.z - sg.x, ey = sg.w - sg.y;
-    float t = ((px - sg.x) * ex + (py - sg.y) * ey) / (ex * ex + ey * ey);
+    const float px = ((cell % te.W) + 0.5f) * c, py = ((cell / te.W) + 0.5f) * c;
+    const float ax = sg.x - te.x0, ay = sg.y - te.y0, bx = sg.z - te.x0, by = sg.w - te.y0;
+    const float ex = bx - ax, ey = by - ay;
+    float t = ((px - ax) * ex + (py - ay) * ey) / (ex * ex + ey * ey);
     t = fminf(1.f, fmaxf(0.f, t));
-    const float dx = sg.x + t * ex - px, dy = sg.y + t * ey - py;
-    return sqrtf(dx * dx + dy * dy) < (reach + 0.7072f * c) * 1.0001f + 1e-5f;
+    const float dx = ax + t * ex - px, dy = ay + t * ey - py;
+    const float slack = 1e-6f * (fabsf(te.x0) + fabsf(te.y0) + (float)max(te.W, te.H) * c);
+    return sqrtf(dx * dx + dy * dy) < (reach + 0.7072f * c) * 1.0001f + 1e-5f + slack;
 }
 
 __global__ void na_seg_count(const TiledEnv* env, const float4* segs, int ns, const Misc* misc, int* seg_start) {
@@ -246,13 +263,16 @@ extern "C" crowd_status crowd_step_noalloc(int32_t n_agents, const float* state_
     NA_TRY(cudaMemsetAsync(misc, 0, sizeof(Misc), s), "clear scratch");
     NA_TRY(cudaMemsetAsync(count, 0, sizeof(int) * C, s), "clear cell counts");
     // per-cell segment lists, checked against the scratch capacity
-    na_reach<<<1, 1024, 0, s>>>((const float4*)agent_params, n_agents, tau_o, misc);
+    na_reach<<<1, 1024, 0, s>>>((const float4*)agent_params, n_agents, tau_o, (const float4*)segments, n_segments,
+                                box[0], box[1], box[2], box[3], misc);
     na_seg_count<<<(C + 255) / 256, 256, 0, s>>>(d_env, (const float4*)segments, n_segments, misc, seg_start);
     na_seg_scan<<<1, 1024, 0, s>>>(d_env, seg_start, misc);
     NA_TRY(cudaGetLastError(), "segment lists");
     Misc h_misc{};
     NA_TRY(cudaMemcpyAsync(&h_misc, misc, sizeof(Misc), cudaMemcpyDeviceToHost, s), "read list size");
     NA_TRY(cudaStreamSynchronize(s), "synchronize");
+    if (h_misc.seg_outside)
+        return api_fail(CROWD_EINVAL, "a segment lies outside the box: the box must contain every segment");
     if (h_misc.seg_total > kNaSegIds)
         return api_fail(CROWD_EINVAL, "%d segment-cell pairs exceed the allocation-free capacity %d", h_misc.seg_total,
                         kNaSegIds);
@@ -289,6 +309,16 @@ extern "C" crowd_status crowd_step_noalloc(int32_t n_agents, const float* state_
     a.err = &misc->err;
     const int max_tiles = ((te.W + te.tx - 1) / te.tx) * ((te.H + te.ty - 1) / te.ty);
     NA_TRY(launch_tiled_step(a, n_agents, max_tiles, s), "allocation-free step");
+    // the device error word of this step (an agent with more segments in
+    // reach than its line buffer holds kept the nearest ones): reported
+    // here, before the next call clears it
+    int h_err = 0;
+    NA_TRY(cudaMemcpyAsync(&h_err, &misc->err, sizeof(int), cudaMemcpyDeviceToHost, s), "read error word");
+    NA_TRY(cudaStreamSynchronize(s), "synchronize");
 #undef NA_TRY
+    if (h_err & kErrObstacleOverflow)
+        return api_fail(CROWD_EDEVICE, "an agent had more than %d static segments in reach; the nearest were kept",
+                        kMaxObstacleLines);
+    if (h_err) return api_fail(CROWD_EDEVICE, "device error word 0x%x", h_err);
     return CROWD_OK;
 }

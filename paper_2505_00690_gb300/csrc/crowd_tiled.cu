@@ -424,8 +424,10 @@ cudaError_t tiled_init(int halo_cap) {
     return e;
 }
 
-cudaError_t launch_tiled_step(const TiledStepArgs& a, int max_agents, int max_tiles, cudaStream_t s) {
+cudaError_t launch_tiled_step(const TiledStepArgs& a, int max_agents, int max_tiles, cudaStream_t s, int* n_kernels) {
+    if (n_kernels) *n_kernels = 0;
     if (a.n_envs == 0) return cudaSuccess;
+    if (n_kernels) *n_kernels = (a.veh_on && a.mode != kTiledStatsOnly) ? 6 : 5;
     const dim3 agrid((max_agents + kCountThreads - 1) / kCountThreads, a.n_envs);
     if (a.veh_on && a.mode != kTiledStatsOnly) tiled_vehicles<<<a.n_envs, kVehicleThreads, 0, s>>>(a);
     tiled_count<<<agrid, kCountThreads, 0, s>>>(a);

@@ -38,7 +38,7 @@ def test_header_declares_the_boundary():
 def test_library_exports_every_declared_symbol(lib):
     for name in declared_functions():
         assert hasattr(lib, name), name
-    assert lib.crowd_abi_version() == 3
+    assert lib.crowd_abi_version() == 4
 
 
 def _params(**kw):
@@ -97,3 +97,30 @@ def test_null_handle_calls_fail_cleanly(lib):
     assert lib.crowd_vehicle_state(None, 0, None, None) == cw.CROWD_EINVAL
     assert lib.crowd_destroy(None) == cw.CROWD_OK
     assert lib.crowd_num_agents(None) == 0
+
+
+def _preceding_comments():
+    """Each declared call with the comment block that comes right before its
+    declaration in the header (the block that documents it)."""
+    out = {}
+    for h in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if not h.endswith(".h"):
+            continue
+        text = open(os.path.join(ROOT, "include", h)).read()
+        for m in re.finditer(r"^\s*[A-Za-z_][\w\s\*]*?\b(crowd_\w+)\s*\(", text, flags=re.M):
+            before = text[:m.start(1)]
+            end = before.rfind("*/")
+            start = before.rfind("/*", 0, end)
+            out[m.group(1)] = before[start:end + 2] if end >= 0 and start >= 0 else ""
+    return out
+
+
+def test_every_call_cites_the_passage_that_defines_it():
+    """Every boundary call names the paper section (or appendix subsection)
+    that defines the operation, or says that the paper has none."""
+    cites = re.compile(r"Sec\. 3\.[1-3]|Appendix \"|[Nn]o counterpart")
+    blocks = _preceding_comments()
+    for name in declared_functions():
+        assert cites.search(blocks.get(name, "")), name
+    for name in ["crowd_create", "crowd_set_goals", "crowd_step", "crowd_read_state"]:
+        assert re.search(r"Sec\. 3\.2", blocks[name]), name

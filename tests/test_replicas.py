@@ -66,3 +66,34 @@ def test_single_process_is_identity():
     assert not dist.is_initialized()
     assert replicas.max_over_ranks(3.5) == 3.5
     assert replicas.aggregate_throughput(100.0, 4.0) == 25.0
+
+
+def _bench(args, env=None):
+    import subprocess
+    import sys
+
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    e = {k: v for k, v in os.environ.items() if k not in ("WORLD_SIZE", "RANK", "LOCAL_RANK")}
+    e.update(env or {})
+    return subprocess.run([sys.executable, os.path.join(root, "bench.py")] + args, capture_output=True, text=True,
+                          timeout=300, cwd=root, env=e)
+
+
+def test_bench_gpus_without_enough_gpus_refuses():
+    """`bench.py --gpus 2` outside a launcher starts one replica process per
+    GPU; with fewer GPUs visible (none here) it exits non-zero instead of
+    timing one GPU and calling it two."""
+    if torch.cuda.is_available() and torch.cuda.device_count() >= 2:
+        pytest.skip("enough GPUs: the spawn path would run the benchmark")
+    r = _bench(["--gpus", "2", "--steps", "1", "--warmup", "0"])
+    assert r.returncode == 2, (r.returncode, r.stderr[-500:])
+    assert "--gpus 2 requested" in r.stderr
+    assert not [l for l in r.stdout.splitlines() if l.startswith("{")]
+
+
+def test_bench_gpus_must_match_launcher_world_size():
+    """Under a launcher, --gpus must equal WORLD_SIZE (else the line's n_gpus
+    and the ranks that ran would disagree)."""
+    r = _bench(["--gpus", "1", "--steps", "1", "--warmup", "0"],
+               env={"WORLD_SIZE": "2", "RANK": "0", "LOCAL_RANK": "0"})
+    assert r.returncode == 2 and "differs from the launcher's WORLD_SIZE 2" in r.stderr, r.stderr[-500:]
