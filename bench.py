@@ -116,13 +116,15 @@ class Clocks:
 
 
 def algorithmic_flops(work):
-    """Algorithmic FP32 operations of the counted work (per-unit costs of the
-    crowd step: 7 per neighbour candidate tested, 35 per agent half-plane,
-    20 per segment half-plane, 12 per segment distance test, 4 per LP check,
-    15 + 10k per 1D sub-solve scanning k previous lines)."""
-    return (7 * work["candidates"] + 35 * work["agent_lines"] + 20 * work["obstacle_lines"]
-            + 12 * work["segment_tests"] + 4 * work["lp_checks"] + 15 * work["lp_solves"]
-            + 10 * work["lp_solve_lines"])
+    """Algorithmic FP32 operations of the counted work, in units the oracle
+    counts identically on the same states (tests/test_work_counts_gpu.py):
+    7 per pair within R (the pairs an exact neighbour search must test; the
+    cells searched hold more, which is not counted), 35 per agent half-plane,
+    20 per segment half-plane, 4 per LP line check, 15 + 10k per 1D sub-solve
+    taking k earlier lines into account.  The fallback's own work is not
+    counted."""
+    return (7 * work["pairs_in_range"] + 35 * work["agent_lines"] + 20 * work["obstacle_lines"]
+            + 4 * work["lp_checks"] + 15 * work["lp_solves"] + 10 * work["lp_solve_lines"])
 
 
 def time_rollouts(cr, rv_dev, init, steps, n_timed, n_warm, stream, flush, dist=False):

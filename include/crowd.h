@@ -94,6 +94,7 @@ typedef struct {
     uint64_t lp_solves;      /* 1D sub-solves (a line violated by the current point) */
     uint64_t lp_solve_lines; /* previous lines scanned by those sub-solves */
     uint64_t fallbacks;      /* agents whose LP was infeasible */
+    uint64_t pairs_in_range; /* candidates j != i within R (FP64 key < R^2): what an exact search must test */
 } crowd_work;
 
 /* Maximum number of neighbours K. */

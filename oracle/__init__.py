@@ -86,7 +86,7 @@ def lib():
             L.or_lp2.restype = C.c_int
             L.or_fallback.argtypes = [C.POINTER(Line), C.c_int, C.c_int, d, d, d, pd, pd, pd]
             L.or_step.argtypes = [i32, pi64, pd, pd, pd, pi32, pi64, pd, C.POINTER(Params), pd, pd, pd, pd,
-                                  pi32, i64, pi64, pd, pd, pi32, pi32, C.c_int]
+                                  pi32, i64, pi64, pd, pd, pi32, pi32, C.c_int, pi64]
             L.or_step.restype = C.c_int
             L.or_collisions.argtypes = [i32, pi64, pd, pi64, pd, pd, pi64, pi64]
             _lib = L
@@ -324,9 +324,14 @@ class OracleScene:
         self.params = scene_params(scene)
         self.dt = self.params.dt
 
-    def step(self, pos, vel, robot_vel=None, sel=None, threads=1, goal=None, kind=None):
+    WORK_KEYS = ("agent_steps", "pairs_in_range", "agent_lines", "obstacle_lines", "lp_checks", "lp_solves",
+                 "lp_solve_lines", "fallbacks")
+
+    def step(self, pos, vel, robot_vel=None, sel=None, threads=1, goal=None, kind=None, work=None):
         """O1-O7 for the selected agents (all when sel is None).  `kind` [N]:
         1 marks vehicles, which keep the given velocity (their lane model's).
+        `work` (a dict, may be None): the step's work items (WORK_KEYS) are
+        added into it.
 
         Returns (pos_out, vel_out, nbrs [N,K] env-local ids -1 padded, status [N]);
         rows of unselected agents are left as NaN / -9."""
@@ -338,6 +343,7 @@ class OracleScene:
         vo = np.full((self.N, 2), np.nan)
         nb = np.full((self.N, max(self.K, 1)), -9, np.int32)
         st = np.full(self.N, -9, np.int32)
+        wk = np.zeros(8, np.int64)
         if sel is None:
             ns, sp = 0, None
         else:
@@ -349,9 +355,12 @@ class OracleScene:
                            _p(pos, C.c_double), _p(vel, C.c_double), _p(goal, C.c_double), _p(rv, C.c_double),
                            None if kd is None else _p(kd, C.c_int32),
                            ns, sp, _p(po, C.c_double), _p(vo, C.c_double), _p(nb, C.c_int32),
-                           _p(st, C.c_int32), int(threads))
+                           _p(st, C.c_int32), int(threads), _p(wk, C.c_int64))
         if rc != 0:
             raise ValueError("oracle step rejected its arguments")
+        if work is not None:
+            for key, v in zip(self.WORK_KEYS, wk):
+                work[key] = work.get(key, 0) + int(v)
         return po, vo, nb[:, : self.K], st
 
     def collisions(self, pos):

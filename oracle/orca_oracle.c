@@ -100,8 +100,10 @@ static int or_cand_cmp(const void* a, const void* b)
 }
 
 /* All agents j != i of the env with key < R^2, ordered by (key, j), first K
- * kept.  ids are env-local.  Returns the count. */
-int or_neighbors(int n, const double* pos, int i, double R, int K, int32_t* out_ids, double* out_keys)
+ * kept.  ids are env-local.  Returns the count; *in_range (if given) gets
+ * the number of agents with key < R^2 before the cap. */
+static int neighbors_counted(int n, const double* pos, int i, double R, int K, int32_t* out_ids, double* out_keys,
+                             int* in_range)
 {
     or_cand* c = (or_cand*)malloc(sizeof(or_cand) * (size_t)(n > 0 ? n : 1));
     int m = 0;
@@ -118,7 +120,13 @@ int or_neighbors(int n, const double* pos, int i, double R, int K, int32_t* out_
         if (out_keys) out_keys[t] = c[t].key;
     }
     free(c);
+    if (in_range) *in_range = m;
     return cnt;
+}
+
+int or_neighbors(int n, const double* pos, int i, double R, int K, int32_t* out_ids, double* out_keys)
+{
+    return neighbors_counted(n, pos, i, R, K, out_ids, out_keys, NULL);
 }
 
 /* Closest point of segment [a,b] to p. */
@@ -428,8 +436,11 @@ static int or_lp1(const or_line* L, int k, double vmax, double prefx, double pre
 
 /* Incremental 2D LP: argmin |v' - pref| over the disk and lines 0..n-1.
  * Returns n when feasible, else the index of the line at which it failed
- * (v holds the last feasible iterate then). */
-int or_lp2(const or_line* L, int n, double vmax, double prefx, double prefy, double* vx, double* vy)
+ * (v holds the last feasible iterate then).  When given, *solves counts the
+ * lines found violated (each starts a 1D solve on it) and *solve_lines the
+ * earlier lines those solves take into account. */
+static int lp2_counted(const or_line* L, int n, double vmax, double prefx, double prefy, double* vx, double* vy,
+                       int64_t* solves, int64_t* solve_lines)
 {
     double pl2 = prefx * prefx + prefy * prefy;
     if (pl2 > vmax * vmax) {
@@ -442,11 +453,17 @@ int or_lp2(const or_line* L, int n, double vmax, double prefx, double prefy, dou
         double s = (*vx - L[k].qx) * L[k].nx + (*vy - L[k].qy) * L[k].ny;
         if (s < 0.0) {
             double nx, ny;
+            if (solves) { *solves += 1; *solve_lines += k; }
             if (!or_lp1(L, k, vmax, prefx, prefy, &nx, &ny)) return k;
             *vx = nx; *vy = ny;
         }
     }
     return n;
+}
+
+int or_lp2(const or_line* L, int n, double vmax, double prefx, double prefy, double* vx, double* vy)
+{
+    return lp2_counted(L, n, vmax, prefx, prefy, vx, vy, NULL, NULL);
 }
 
 /* ---------------------------------------------------------------- O6 ---- */
@@ -513,13 +530,18 @@ void or_fallback(const or_line* L, int n, int n_hard, double vmax, double prefx,
  *   NULL); status_out [N]: 0 LP feasible, 1 fallback, 2 robot, 3 vehicle (may be NULL).
  * kind [N] (may be NULL): 1 marks a vehicle, which keeps its given velocity
  * (set by its lane model) and which the others avoid with full
- * responsibility. 
+ * responsibility.
+ * work [8] (may be NULL): work items of this step added in, for the operation
+ * count of the step: agent updates, pairs j != i within R (key < R^2), agent
+ * lines, segment lines, LP line checks, LP 1D solves, earlier lines those
+ * solves take into account, infeasible LPs (fallbacks).
  * Returns 0, or -1 on bad arguments. */
 int or_step(int32_t n_envs, const int64_t* env_start, const double* radius, const double* vmax,
             const double* pref_speed, const int32_t* robot_index, const int64_t* seg_start,
             const double* segs, const or_params* prm, const double* pos, const double* vel,
             const double* goal, const double* robot_vel, const int32_t* kind, int64_t n_sel, const int64_t* sel,
-            double* pos_out, double* vel_out, int32_t* nbr_out, int32_t* status_out, int n_threads)
+            double* pos_out, double* vel_out, int32_t* nbr_out, int32_t* status_out, int n_threads,
+            int64_t* work)
 {
     if (!prm || prm->max_neighbors < 0 || prm->max_neighbors > OR_MAX_K) return -1;
     const int K = prm->max_neighbors;
@@ -527,9 +549,12 @@ int or_step(int32_t n_envs, const int64_t* env_start, const double* radius, cons
     int64_t n_total = env_start[n_envs];
     int64_t count = sel ? n_sel : n_total;
     int bad = 0;
+    int64_t w_steps = 0, w_pairs = 0, w_alines = 0, w_olines = 0, w_checks = 0, w_solves = 0, w_solve_lines = 0,
+            w_fallbacks = 0;
 #ifdef _OPENMP
     if (n_threads > 0) omp_set_num_threads(n_threads);
-#pragma omp parallel for schedule(dynamic, 8) reduction(| : bad)
+#pragma omp parallel for schedule(dynamic, 8) \
+    reduction(| : bad) reduction(+ : w_steps, w_pairs, w_alines, w_olines, w_checks, w_solves, w_solve_lines, w_fallbacks)
 #endif
     for (int64_t t = 0; t < count; ++t) {
         int64_t g = sel ? sel[t] : t;
@@ -550,7 +575,10 @@ int or_step(int32_t n_envs, const int64_t* env_start, const double* radius, cons
 #define OR_VEL(j, c) ((j) == robot ? robot_vel[2 * e + (c)] : vel[2 * (base + (j)) + (c)])
 
         int32_t ids[OR_MAX_K];
-        int nn = or_neighbors(n, P, i, prm->neighbor_dist, K, ids, NULL);
+        int in_range = 0;
+        int nn = neighbors_counted(n, P, i, prm->neighbor_dist, K, ids, NULL, &in_range);
+        w_steps += 1;
+        w_pairs += in_range;
         if (nbr_out) {
             for (int k = 0; k < K; ++k) nbr_out[g * K + k] = k < nn ? ids[k] : -1;
         }
@@ -597,10 +625,17 @@ int or_step(int32_t n_envs, const int64_t* env_start, const double* radius, cons
                               prm->tau, prm->dt, alpha, i, j, &L[no + k]);
             }
             int nl = no + nn;
-            if (or_lp2(L, nl, vmax[g], prefx, prefy, &nvx, &nvy) < nl) {
+            int64_t solves = 0, solve_lines = 0;
+            if (lp2_counted(L, nl, vmax[g], prefx, prefy, &nvx, &nvy, &solves, &solve_lines) < nl) {
                 or_fallback(L, nl, no, vmax[g], prefx, prefy, &nvx, &nvy, NULL);
                 status = 1;
+                w_fallbacks += 1;
             }
+            w_alines += nn;
+            w_olines += no;
+            w_checks += nl;
+            w_solves += solves;
+            w_solve_lines += solve_lines;
             free(L);
             free(oids);
         }
@@ -610,6 +645,16 @@ int or_step(int32_t n_envs, const int64_t* env_start, const double* radius, cons
         pos_out[2 * g + 1] = P[2 * i + 1] + prm->dt * nvy;
         if (status_out) status_out[g] = status;
 #undef OR_VEL
+    }
+    if (work) {
+        work[0] += w_steps;
+        work[1] += w_pairs;
+        work[2] += w_alines;
+        work[3] += w_olines;
+        work[4] += w_checks;
+        work[5] += w_solves;
+        work[6] += w_solve_lines;
+        work[7] += w_fallbacks;
     }
     return bad ? -1 : 0;
 }

@@ -53,7 +53,7 @@ class crowd_env_stats(C.Structure):
 class crowd_work(C.Structure):
     _fields_ = [(n, C.c_uint64) for n in ("agent_steps", "candidates", "agent_lines", "obstacle_lines",
                                           "segment_tests", "lp_checks", "lp_solves", "lp_solve_lines",
-                                          "fallbacks")]
+                                          "fallbacks", "pairs_in_range")]
 
 
 class crowd_tuning(C.Structure):

@@ -83,7 +83,7 @@ __device__ __forceinline__ float2 advance_goal(const GoalQueue& gq, int g, int e
 // Per-thread work tallies (only reported when counting is on).
 struct Tally {
     unsigned long long agent_steps = 0, candidates = 0, agent_lines = 0, obstacle_lines = 0, segment_tests = 0,
-                       lp_checks = 0, lp_solves = 0, lp_solve_lines = 0, fallbacks = 0;
+                       lp_checks = 0, lp_solves = 0, lp_solve_lines = 0, fallbacks = 0, pairs_in_range = 0;
 };
 
 template <int KMAX>
@@ -233,6 +233,7 @@ __device__ __forceinline__ void select_neighbors(const Src& src, int cx, int cy,
         if (d2 < R2hi) {
             if (d2 == 0.f && src.cand_id(cu) == self) continue;
             if (d2 > R2lo && !(rank_key(xi, yi, o.x, o.y) < R2bits)) continue;
+            ++w.pairs_in_range;
             top.insert(((unsigned long long)__float_as_uint(d2) << 32) | (unsigned)cu);
         }
     }
@@ -445,11 +446,12 @@ __device__ __forceinline__ float2 solve_velocity(const AgentParams& a, const Age
 // Warp-reduce the tallies and add them to the global counters.
 __device__ __forceinline__ void flush_tally(const Tally& tally, WorkCount* work) {
     unsigned long long* dst = &work->agent_steps;
-    const unsigned long long vals[9] = {tally.agent_steps, tally.candidates, tally.agent_lines,
-                                        tally.obstacle_lines, tally.segment_tests, tally.lp_checks,
-                                        tally.lp_solves, tally.lp_solve_lines, tally.fallbacks};
+    const unsigned long long vals[10] = {tally.agent_steps, tally.candidates, tally.agent_lines,
+                                         tally.obstacle_lines, tally.segment_tests, tally.lp_checks,
+                                         tally.lp_solves, tally.lp_solve_lines, tally.fallbacks,
+                                         tally.pairs_in_range};
 #pragma unroll
-    for (int q = 0; q < 9; ++q) {
+    for (int q = 0; q < 10; ++q) {
         unsigned long long v = vals[q];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);

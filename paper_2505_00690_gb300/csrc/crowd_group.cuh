@@ -226,6 +226,7 @@ __device__ __forceinline__ void group_select(const Grp<G>& g, const Src& src, in
                 const int j = src.cand_id(u);
                 if (j == self) continue;
                 if (d2 > R2lo && !(rank_key(xi, yi, o.x, o.y) < R2bits)) continue;
+                ++w.pairs_in_range;
                 top.insert(((unsigned long long)__float_as_uint(d2) << 32) | (unsigned)j);
             }
         }

@@ -83,7 +83,7 @@ struct EnvStats {
 // Work counters (mirrors crowd_work of the public header).
 struct WorkCount {
     unsigned long long agent_steps, candidates, agent_lines, obstacle_lines, segment_tests, lp_checks, lp_solves,
-        lp_solve_lines, fallbacks;
+        lp_solve_lines, fallbacks, pairs_in_range;
 };
 
 // Static grid over an environment's segments with, per cell, the ascending
