@@ -374,13 +374,18 @@ class OracleScene:
         return a, s
 
 
-def rollout(scene, steps, threads=1, record=False):
+def rollout(scene, steps, threads=1, record=False, fp32_state=False):
     """Free-running FP64 rollout from the scene's initial state.
 
     O8 statistics over the non-robot agents: collision events summed over the
     post-integration states of every step (pairs involving the robot count),
     mean speed over agents and steps, goal reach (first step with
     |g - p| <= r), mean reach time in seconds and fraction reached.
+
+    fp32_state: hold the state between steps in FP32, the format the crowd
+    library's boundary stores and exchanges it in (each step still computes
+    in FP64 from that state, as under teacher forcing); the statistics are
+    then taken on the rounded state.
     """
     o = OracleScene(scene)
     pos = _f64(scene.pos).copy()
@@ -395,6 +400,9 @@ def rollout(scene, steps, threads=1, record=False):
     states = []
     for k in range(steps):
         pos, vel, _, _ = o.step(pos, vel, scene.robot_vel_at(k), threads=threads)
+        if fp32_state:
+            pos = pos.astype(np.float32).astype(np.float64)
+            vel = vel.astype(np.float32).astype(np.float64)
         a, s = o.collisions(pos)
         coll_a += int(a.sum())
         coll_s += int(s.sum())
