@@ -317,13 +317,20 @@ crowd_status crowd_read_launches(crowd_t h, int64_t* out);
  *                  (warps) apart in cell order, which spreads a crowded
  *                  region over all warps.
  * block_threads 0 means one group of lanes per agent of the largest
- * environment, at most 512 threads. */
+ * environment, at most 512 threads.
+ * The tiled path (environments of more than 2048 agents):
+ *   tiled_queue:   1 = one persistent launch per step whose warps take work
+ *                  items (32 agents in cell order of one environment) from a
+ *                  counter shared by all tiled environments (the default);
+ *                  0 = one CTA per tile of cells, its halo staged in shared
+ *                  memory.  Both give the same bits. */
 typedef struct {
     int32_t block_threads;
     int32_t coop_fallback;
     int32_t cell_split;
     int32_t lanes_per_agent;
     int32_t agent_order;
+    int32_t tiled_queue;
 } crowd_tuning;
 
 /* Read / set the launch shape.  No counterpart in the paper (this
@@ -335,7 +342,8 @@ crowd_status crowd_set_tuning(crowd_t h, const crowd_tuning* t);
  * Time every tuning candidate (one lane per agent: block_threads
  * default/64/128/256/512 x coop_fallback 0 and 2 x cell_split 1-3 x
  * agent_order; 2, 4 and 8 lanes per agent: the default block and 512 threads
- * x cell_split 1-2) over n_steps steps of length dt from the current state, keep
+ * x cell_split 1-2; with tiled environments, tiled_queue 0 and 1) over
+ * n_steps steps of length dt from the current state, keep
  * the fastest, and restore the state, statistics and counters.  Waits for the
  * stream; allocates temporary device memory.  `chosen` may be NULL. */
 crowd_status crowd_autotune(crowd_t h, float dt, int32_t n_steps, crowd_tuning* chosen);
@@ -512,7 +520,7 @@ const char* crowd_last_error(void);
 
 /* Library ABI version (increments on any signature change).
  * No counterpart in the paper. */
-int32_t crowd_abi_version(void);  /* 4: adds crowd_read_launches */
+int32_t crowd_abi_version(void);  /* 5: crowd_read_launches, crowd_tuning.tiled_queue */
 
 #ifdef __cplusplus
 }

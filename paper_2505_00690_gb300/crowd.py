@@ -58,7 +58,7 @@ class crowd_work(C.Structure):
 
 class crowd_tuning(C.Structure):
     _fields_ = [("block_threads", C.c_int32), ("coop_fallback", C.c_int32), ("cell_split", C.c_int32),
-                ("lanes_per_agent", C.c_int32), ("agent_order", C.c_int32)]
+                ("lanes_per_agent", C.c_int32), ("agent_order", C.c_int32), ("tiled_queue", C.c_int32)]
 
 
 _lib = None
@@ -216,11 +216,12 @@ def crowd_get_tuning(h):
     t = crowd_tuning()
     _check(load().crowd_get_tuning(h, C.byref(t)))
     return dict(block_threads=t.block_threads, coop_fallback=t.coop_fallback, cell_split=t.cell_split,
-                lanes_per_agent=t.lanes_per_agent, agent_order=t.agent_order)
+                lanes_per_agent=t.lanes_per_agent, agent_order=t.agent_order, tiled_queue=t.tiled_queue)
 
 
-def crowd_set_tuning(h, block_threads=0, coop_fallback=0, cell_split=1, lanes_per_agent=1, agent_order=0):
-    t = crowd_tuning(block_threads, coop_fallback, cell_split, lanes_per_agent, agent_order)
+def crowd_set_tuning(h, block_threads=0, coop_fallback=0, cell_split=1, lanes_per_agent=1, agent_order=0,
+                     tiled_queue=1):
+    t = crowd_tuning(block_threads, coop_fallback, cell_split, lanes_per_agent, agent_order, tiled_queue)
     _check(load().crowd_set_tuning(h, C.byref(t)))
 
 
@@ -228,7 +229,7 @@ def crowd_autotune(h, dt, n_steps):
     t = crowd_tuning()
     _check(load().crowd_autotune(h, C.c_float(dt), int(n_steps), C.byref(t)))
     return dict(block_threads=t.block_threads, coop_fallback=t.coop_fallback, cell_split=t.cell_split,
-                lanes_per_agent=t.lanes_per_agent, agent_order=t.agent_order)
+                lanes_per_agent=t.lanes_per_agent, agent_order=t.agent_order, tiled_queue=t.tiled_queue)
 
 
 def crowd_reset_stats(h):

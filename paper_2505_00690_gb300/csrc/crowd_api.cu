@@ -126,7 +126,7 @@ struct crowd_ctx {
     int res_max_agents = 0;
     int res_max_work = 0;  // largest count of solved (non-robot) agents of a resident environment
     int block = 0, grid = 0;  // resident launch shape for `tune`
-    Tuning tune{0, 0, 1, 1, 0};
+    Tuning tune{0, 0, 1, 1, 0, 1};
     int sms = 0;
 
     // tiled path: larger environments (or all, with CROWD_FLAG_FORCE_TILED)
@@ -145,6 +145,10 @@ struct crowd_ctx {
     SegGrid* seg_grid = nullptr;
     long long* d_step = nullptr;
     cudaStream_t cap_stream = nullptr;
+    int* item_start = nullptr;  // [n_tiled + 1] work items (32 sorted slots) of the persistent update
+    int n_items = 0;
+    int* tqueue = nullptr;      // work-item counter of the persistent update
+    int queue_grid = 0;         // its CTAs: as many as fit on the GPU
     cudaGraphExec_t graph = nullptr;
     int64_t graph_kernels = 0;    // kernel launches one replay of `graph` performs
     int64_t kernel_launches = 0;  // kernels this handle's steps enqueued (graph replays by their kernels)
@@ -165,7 +169,8 @@ struct crowd_ctx {
                         veh_start, veh_agent, veh_lane, veh_s, veh_v, veh_par_a, veh_par_b, lane_pts, lane_start,
                         lane_cum, veh_pref, ep_steps, ep_state, ep_goal, ep_gidx, ep_veh, ep_mask, pool_start, pool,
                         segs, robot_vel, nbr, reach, stats, work, tenvs, state_b, sorted_pv, key, rank,
-                        count, start, sorted_id, seg_cell_start, seg_cell_ids, seg_grid, d_step};
+                        count, start, sorted_id, seg_cell_start, seg_cell_ids, seg_grid, d_step, item_start,
+                        tqueue};
         for (void* q : ptrs)
             if (q) cudaFree(q);
     }
@@ -467,6 +472,7 @@ void build_tiled_env(int e, int base, int n, int seg0, int ns, int robot, const 
 // Launch shape of the resident kernel for a tuning: block threads (0: one per
 // agent of the largest environment, 64..512) and as many CTAs as fit.
 void apply_tuning(crowd_t h, const Tuning& t) {
+    if (t.tiled_queue != h->tune.tiled_queue) drop_graph(h);  // cached tiled graphs hold the update kernel
     h->tune = t;
     // default: one thread per agent, or one group of lanes per solved agent
     // (the robot is integrated apart in that mode)
@@ -607,6 +613,11 @@ TiledStepArgs tiled_args(crowd_t h, float dt, const float2* rv, int s, int n_ste
     a.sorted_pv = h->sorted_pv;
     a.sorted_id = h->sorted_id;
     a.halo_cap = h->halo_cap;
+    a.use_queue = h->tune.tiled_queue;
+    a.item_start = h->item_start;
+    a.n_items = h->n_items;
+    a.queue = h->tqueue;
+    a.queue_grid = h->queue_grid;
     a.R = h->p.neighbor_dist;
     a.dt = dt;
     a.tau = h->p.time_horizon;
@@ -734,7 +745,7 @@ crowd_status tiled_steps(crowd_t h, float dt, const float2* rv, int n_steps, boo
 
 extern "C" {
 
-int32_t crowd_abi_version(void) { return 4; }  // 4: crowd_read_launches
+int32_t crowd_abi_version(void) { return 5; }  // 5: crowd_read_launches, crowd_tuning.tiled_queue
 
 const char* crowd_last_error(void) { return g_last_error.c_str(); }
 
@@ -864,6 +875,11 @@ crowd_status crowd_create(int32_t n_envs, const int32_t* agents_per_env, const f
         h->tiled_max_tiles = std::max(h->tiled_max_tiles, ((te.W + te.tx - 1) / te.tx) * ((te.H + te.ty - 1) / te.ty));
         h->h_tenvs.push_back(te);
     }
+    // work items of the persistent update: kQueueItem consecutive sorted
+    // slots of one environment
+    std::vector<int> item_start(1, 0);
+    for (const TiledEnv& te : h->h_tenvs) item_start.push_back(item_start.back() + (te.n + kQueueItem - 1) / kQueueItem);
+    h->n_items = item_start.back();
     std::vector<SegGrid> seg_grids(std::max(n_envs, 1));
     int seg_off = total_cells;
     for (int e : order) {
@@ -901,6 +917,8 @@ crowd_status crowd_create(int32_t n_envs, const int32_t* agents_per_env, const f
         ALLOC(count, total_cells);
         ALLOC(start, total_cells);
         ALLOC(d_step, 1);
+        ALLOC(item_start, item_start.size());
+        ALLOC(tqueue, 1);
     }
     ALLOC(env_start, n_envs + 1);
     ALLOC(seg_start, n_envs + 1);
@@ -928,6 +946,7 @@ crowd_status crowd_create(int32_t n_envs, const int32_t* agents_per_env, const f
         {h->robot_index, robot.data(), sizeof(int) * n_envs},
         {h->order, order.data(), sizeof(int) * order.size()},
         {h->tenvs, h->h_tenvs.data(), sizeof(TiledEnv) * h->h_tenvs.size()},
+        {h->item_start, item_start.data(), h->n_tiled ? sizeof(int) * item_start.size() : 0},
         {h->seg_cell_start, seg_cell_start.data(), sizeof(int) * seg_cell_start.size()},
         {h->seg_cell_ids, seg_cell_ids.data(), sizeof(int) * seg_cell_ids.size()},
         {h->seg_grid, seg_grids.data(), sizeof(SegGrid) * n_envs},
@@ -980,6 +999,14 @@ crowd_status crowd_create(int32_t n_envs, const int32_t* agents_per_env, const f
         return bail(CROWD_ECUDA);
     }
     h->sms = sms;
+    if (h->n_tiled) {
+        const int per_sm = tiled_queue_blocks_per_sm(p->max_neighbors);
+        if (per_sm < 1) {
+            cuda_fail(cudaGetLastError(), "occupancy of the persistent tiled update");
+            return bail(CROWD_ECUDA);
+        }
+        h->queue_grid = per_sm * sms;
+    }
     apply_tuning(h, h->tune);
 
     if ((e = cudaStreamSynchronize(h->stream)) != cudaSuccess) {
@@ -1456,6 +1483,7 @@ crowd_status crowd_get_tuning(crowd_t h, crowd_tuning* out) {
     out->cell_split = h->tune.cell_split;
     out->lanes_per_agent = h->tune.lanes;
     out->agent_order = h->tune.order;
+    out->tiled_queue = h->tune.tiled_queue;
     return CROWD_OK;
 }
 
@@ -1471,7 +1499,8 @@ crowd_status crowd_set_tuning(crowd_t h, const crowd_tuning* t) {
         return fail(CROWD_EINVAL, "lanes_per_agent must be 1, 2, 4 or 8");
     if (t->coop_fallback < 0 || t->coop_fallback > 2) return fail(CROWD_EINVAL, "coop_fallback must be 0, 1 or 2");
     if (t->agent_order != 0 && t->agent_order != 1) return fail(CROWD_EINVAL, "agent_order must be 0 or 1");
-    apply_tuning(h, Tuning{t->block_threads, t->coop_fallback, t->cell_split, lanes, t->agent_order});
+    if (t->tiled_queue != 0 && t->tiled_queue != 1) return fail(CROWD_EINVAL, "tiled_queue must be 0 or 1");
+    apply_tuning(h, Tuning{t->block_threads, t->coop_fallback, t->cell_split, lanes, t->agent_order, t->tiled_queue});
     return CROWD_OK;
 }
 
@@ -1480,7 +1509,7 @@ crowd_status crowd_autotune(crowd_t h, float dt, int32_t n_steps, crowd_tuning* 
     crowd_status st = check_handle(h);
     if (st) return st;
     if (!(dt > 0.f) || !std::isfinite(dt) || n_steps < 1) return fail(CROWD_EINVAL, "dt > 0 and n_steps >= 1 required");
-    if (h->n_res && h->N) {
+    if ((h->n_res || h->n_tiled) && h->N) {
         // save everything a trial step touches, time each candidate, restore
         float4* saved = nullptr;
         EnvStats* saved_stats = nullptr;
@@ -1535,15 +1564,26 @@ crowd_status crowd_autotune(crowd_t h, float dt, int32_t n_steps, crowd_tuning* 
         // (capped at 512 threads) or 512 threads
         std::vector<Tuning> cands;
         const int blocks[] = {0, 64, 128, 256, 512};
-        for (int bi = 0; bi < 5; ++bi)
-            for (int coop : {0, 2})
-                for (int split = 1; split <= 3; ++split)
-                    for (int order = 0; order <= 1; ++order)
-                        cands.push_back(Tuning{blocks[bi], coop, split, 1, order});
-        for (int lanes : {2, 4, 8})
-            for (int split = 1; split <= 2; ++split) {
-                cands.push_back(Tuning{0, 0, split, lanes, 0});
-                cands.push_back(Tuning{512, 0, split, lanes, 0});
+        const int tq = before.tiled_queue;
+        if (h->n_res) {
+            for (int bi = 0; bi < 5; ++bi)
+                for (int coop : {0, 2})
+                    for (int split = 1; split <= 3; ++split)
+                        for (int order = 0; order <= 1; ++order)
+                            cands.push_back(Tuning{blocks[bi], coop, split, 1, order, tq});
+            for (int lanes : {2, 4, 8})
+                for (int split = 1; split <= 2; ++split) {
+                    cands.push_back(Tuning{0, 0, split, lanes, 0, tq});
+                    cands.push_back(Tuning{512, 0, split, lanes, 0, tq});
+                }
+        }
+        // the tiled path's update kernel (persistent work queue or one CTA
+        // per tile), with the resident shape as it stands
+        if (h->n_tiled)
+            for (int q : {0, 1}) {
+                Tuning t = before;
+                t.tiled_queue = q;
+                cands.push_back(t);
             }
         // one timed run (after an untimed one) of a candidate from the saved start
         auto time_once = [&](const Tuning& t, float& ms) {
@@ -1554,7 +1594,11 @@ crowd_status crowd_autotune(crowd_t h, float dt, int32_t n_steps, crowd_tuning* 
                 if (e != cudaSuccess) break;
                 if (rep == 1) e = cudaEventRecord(t0, h->stream);
                 if (e != cudaSuccess) break;
-                if (resident_steps(h, dt, nullptr, n_steps, false, tau_o, h->stream) != CROWD_OK) {
+                if (h->n_res && resident_steps(h, dt, nullptr, n_steps, false, tau_o, h->stream) != CROWD_OK) {
+                    e = cudaErrorLaunchFailure;
+                    break;
+                }
+                if (h->n_tiled && tiled_steps(h, dt, nullptr, n_steps, false, tau_o) != CROWD_OK) {
                     e = cudaErrorLaunchFailure;
                     break;
                 }

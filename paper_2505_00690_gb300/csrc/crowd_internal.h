@@ -150,6 +150,7 @@ struct Tuning {
     int cell_split;
     int lanes;          // lanes per agent: 1, 2, 4 or 8
     int order;          // agent order over the warps (one lane per agent only)
+    int tiled_queue;    // tiled path: 1 = persistent work-queue update, 0 = one CTA per tile
 };
 
 // One large environment of the tiled path (static uniform grid, cell >= R).
@@ -171,6 +172,10 @@ constexpr int kTileMax = 8;
 constexpr int kTiledSpanMax = 2;
 // Threads of a CTA of the tiled update kernel.
 constexpr int kTiledUpdateThreads = 256;
+// Threads of a CTA of the persistent (work-queue) tiled update kernel, and
+// agents per work item (one warp).
+constexpr int kQueueThreads = 128;
+constexpr int kQueueItem = 32;
 // Cells of R / 2 are used when the tiled agents of a handle number at least
 // this many rounds of kTiledUpdateThreads on every SM.
 constexpr int kFineCellRounds = 4;
@@ -221,6 +226,15 @@ struct TiledStepArgs {
     float4* sorted_pv;        // [N] scratch: state in cell order
     int* sorted_id;           // [N] scratch: environment-local index of each sorted slot
     int halo_cap;             // agents the update kernel stages in shared memory
+    // persistent update (use_queue != 0): work items of 32 consecutive sorted
+    // slots of one environment, item_start[t] the first item of tiled
+    // environment t ([n_envs + 1]), taken from the counter *queue (zeroed by
+    // tiled_scan) by the warps of queue_grid CTAs
+    int use_queue;
+    const int* item_start;
+    int n_items;
+    int* queue;
+    int queue_grid;
     float R, dt, tau, tau_o, robot_alpha;
     int K;
     int seg_vd;               // 1: velocity-dependent segment half-planes
@@ -237,6 +251,9 @@ struct TiledStepArgs {
 constexpr int kHaloCap = 3072;
 
 size_t tiled_smem_bytes(int halo_cap);
+// CTAs of the persistent tiled update kernel for neighbour cap K that fit on
+// one SM (0 on error).
+int tiled_queue_blocks_per_sm(int K);
 // One-time kernel attributes of the tiled path (before any capture).
 cudaError_t tiled_init(int halo_cap);
 // Enqueue one thread setting the device step counter.

@@ -25,6 +25,8 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <algorithm>
+
 #include "../../include/crowd.h"
 #include "crowd_agent.cuh"
 #include "crowd_internal.h"
@@ -91,6 +93,7 @@ __global__ void __launch_bounds__(kScanThreads) tiled_scan(TiledStepArgs a) {
     const int C = te.W * te.H;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (threadIdx.x == 0) carry = te.base;
+    if (blockIdx.x == 0 && threadIdx.x == 0 && a.queue) *a.queue = 0;  // work items of this step's update
     __syncthreads();
     for (int c0 = 0; c0 < C; c0 += blockDim.x) {
         const int c = c0 + threadIdx.x;
@@ -339,6 +342,70 @@ __global__ void __launch_bounds__(kUpdateThreads) tiled_update(TiledStepArgs a) 
     }
 }
 
+// Warp sums (all lanes get the total).
+__device__ __forceinline__ unsigned long long warp_sum(unsigned long long v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Persistent form of the update (one launch for every tiled environment):
+// as many CTAs as fit on the GPU, and every warp takes work items from one
+// counter shared by all environments, an item being kQueueItem consecutive
+// sorted slots (agents in cell order) of one environment.  Candidates and
+// neighbours are read from the step's global arrays through L1/L2 (an item's
+// agents share most of their candidate cells).  Warps never wait for one
+// another: a crowded item holds up only its own warp, where a CTA per tile
+// held its whole CTA until its slowest warp was done, and environments of
+// any size share the launch.  The per-agent work is tile_agent's, so the
+// results are those of tiled_update bit for bit.
+#ifndef CROWD_QUEUE_MINB
+#define CROWD_QUEUE_MINB 1
+#endif
+template <int KMAX>
+__global__ void __launch_bounds__(kQueueThreads, CROWD_QUEUE_MINB) tiled_update_queue(TiledStepArgs a) {
+    const int lane = threadIdx.x & 31;
+    const AgentParams ap{a.R, a.dt, a.tau, a.tau_o, a.robot_alpha, a.K, a.segs, a.err, a.seg_vd};
+    Tally w;
+    for (;;) {
+        int item = 0;
+        if (lane == 0) item = atomicAdd(a.queue, 1);
+        item = __shfl_sync(0xffffffffu, item, 0);
+        if (item >= a.n_items) break;
+        int lo = 0, hi = a.n_envs - 1;  // environment of the item
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (__ldg(&a.item_start[mid]) <= item) lo = mid;
+            else hi = mid - 1;
+        }
+        const TiledEnv te = a.envs[lo];
+        const int q = (item - __ldg(&a.item_start[lo])) * kQueueItem + lane;
+        unsigned long long ca = 0, cs = 0;
+        double speed = 0.0;
+        if (q < te.n) {
+            const GlobalSource src{a.sorted_pv, a.sorted_id, a.start + te.co, te.W};
+            tile_agent<KMAX>(a, ap, te, src, te.base + q, w, ca, cs, speed);
+        }
+        if (a.stats) {
+            ca = warp_sum(ca);
+            cs = warp_sum(cs);
+            speed = warp_sum(speed);
+            if (lane == 0) {
+                EnvStats* st = a.stats + te.e;
+                if (ca) atomicAdd(&st->agent_collisions, ca);
+                if (cs) atomicAdd(&st->segment_collisions, cs);
+                if (speed != 0.0) atomicAdd(&st->speed_sum, speed);
+            }
+        }
+    }
+    if (a.work) flush_tally(w, a.work);
+}
+
 constexpr int kVehicleThreads = 256;
 
 // Cars of tiled environment blockIdx.x (at most CROWD_MAX_VEHICLES_PER_ENV),
@@ -400,8 +467,23 @@ __global__ void tiled_finish_step(TiledStepArgs a) {
 
 template <int KMAX>
 cudaError_t update_k(const TiledStepArgs& a, int max_tiles, cudaStream_t s) {
-    tiled_update<KMAX><<<dim3(max_tiles, a.n_envs), kUpdateThreads, tiled_smem_bytes(a.halo_cap), s>>>(a);
+    if (a.use_queue) {
+        const int warps = kQueueThreads / 32;
+        const int grid = std::max(1, std::min(a.queue_grid, (a.n_items + warps - 1) / warps));
+        tiled_update_queue<KMAX><<<grid, kQueueThreads, 0, s>>>(a);
+    } else {
+        tiled_update<KMAX><<<dim3(max_tiles, a.n_envs), kUpdateThreads, tiled_smem_bytes(a.halo_cap), s>>>(a);
+    }
     return cudaGetLastError();
+}
+
+template <int KMAX>
+int queue_blocks() {
+    int n = 0;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, tiled_update_queue<KMAX>, kQueueThreads, 0) ==
+                   cudaSuccess
+               ? n
+               : 0;
 }
 
 }  // namespace
@@ -414,6 +496,15 @@ cudaError_t launch_set_step(long long* p, long long value, cudaStream_t s) {
 }
 
 size_t tiled_smem_bytes(int halo_cap) { return (size_t)halo_cap * (sizeof(float4) + sizeof(int)); }
+
+int tiled_queue_blocks_per_sm(int K) {
+    switch (resident_kmax(K)) {
+        case 8: return queue_blocks<8>();
+        case 10: return queue_blocks<10>();
+        case 16: return queue_blocks<16>();
+        default: return queue_blocks<32>();
+    }
+}
 
 cudaError_t tiled_init(int halo_cap) {
     const int smem = (int)tiled_smem_bytes(halo_cap);

@@ -38,7 +38,7 @@ def test_header_declares_the_boundary():
 def test_library_exports_every_declared_symbol(lib):
     for name in declared_functions():
         assert hasattr(lib, name), name
-    assert lib.crowd_abi_version() == 4
+    assert lib.crowd_abi_version() == 5
 
 
 def _params(**kw):
