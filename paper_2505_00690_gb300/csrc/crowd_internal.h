@@ -176,6 +176,14 @@ constexpr int kTiledUpdateThreads = 256;
 // agents per work item (one warp).
 constexpr int kQueueThreads = 128;
 constexpr int kQueueItem = 32;
+// CTAs of the persistent update per SM the compiler budgets registers for
+// (65,536 / (5 x 128) = 102 a thread): 20 warps per SM ran the
+// 16 x 20,000 crowd 13 % faster than 16 warps at 128 registers, and 24 or
+// 32 warps (80 / 64 registers, more spills) no faster
+#ifndef CROWD_QUEUE_MINB
+#define CROWD_QUEUE_MINB 5
+#endif
+constexpr int kQueueMinBlocks = CROWD_QUEUE_MINB;
 // Cells of R / 2 are used when the tiled agents of a handle number at least
 // this many rounds of kTiledUpdateThreads on every SM.
 constexpr int kFineCellRounds = 4;

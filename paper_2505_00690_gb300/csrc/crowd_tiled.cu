@@ -216,7 +216,8 @@ __device__ __forceinline__ void tile_agent(const TiledStepArgs& a, const AgentPa
     }
 
     NbList<KMAX> nb;
-    select_neighbors<KMAX>(src, cx, cy, te.W, te.H, i, me, ap.R, ap.K, nb, w, te.span);
+    select_neighbors<KMAX>(src, CellGeom{te.x0, te.y0, te.inv_c}, cx, cy, te.W, te.H, i, me, ap.R, ap.K, nb, w,
+                           te.span);
     if (a.nbr_out) {
         int* out = a.nbr_out + (size_t)g * ap.K;
 #pragma unroll
@@ -364,11 +365,8 @@ __device__ __forceinline__ double warp_sum(double v) {
 // held its whole CTA until its slowest warp was done, and environments of
 // any size share the launch.  The per-agent work is tile_agent's, so the
 // results are those of tiled_update bit for bit.
-#ifndef CROWD_QUEUE_MINB
-#define CROWD_QUEUE_MINB 1
-#endif
 template <int KMAX>
-__global__ void __launch_bounds__(kQueueThreads, CROWD_QUEUE_MINB) tiled_update_queue(TiledStepArgs a) {
+__global__ void __launch_bounds__(kQueueThreads, kQueueMinBlocks) tiled_update_queue(TiledStepArgs a) {
     const int lane = threadIdx.x & 31;
     const AgentParams ap{a.R, a.dt, a.tau, a.tau_o, a.robot_alpha, a.K, a.segs, a.err, a.seg_vd};
     Tally w;
