@@ -18,10 +18,6 @@
 #include "orca_device.cuh"
 #include "philox.cuh"
 
-#ifndef CROWD_SEL_BUF
-#define CROWD_SEL_BUF 0
-#endif
-
 namespace crowd {
 
 // Agents whose LP was infeasible, queued with their lines for the
@@ -180,41 +176,10 @@ __device__ __forceinline__ float box_dist2(float px, float py, float4 s) {
     return dx * dx + dy * dy;
 }
 
-// Placement of a uniform grid: agent at (x, y) lies in cell
-// clamp(floor((x - x0) inv_c)), clamp(floor((y - y0) inv_c)).
-struct CellGeom {
-    float x0, y0, inv_c;
-};
-
-// Cells [a, b] of row yy of the (2 span + 1)^2 block [xa, xb] around the
-// agent's cell (cx, cy) whose points can lie within R of the agent at
-// (mx, my): the row's y-distance to the agent, less a margin for the FP32
-// rounding of the cell edges, leaves a half-width w = sqrt(R^2 - dy^2) in x,
-// and the cells of mx - w and mx + w come from the same clamped floor map
-// that placed the agents, which is monotone, so no cell holding an agent
-// within R is dropped (a cell outside the grid's box is its border cell,
-// whose points extend to infinity; the edge nearest the agent is what the
-// distance takes).  An empty range (b = a - 1) when the row is farther.
-__device__ __forceinline__ int2 clip_row(const CellGeom& g, int W, float mx, float my, int cy, int yy, int xa, int xb,
-                                         float R2, float margin) {
-    const float c = 1.f / g.inv_c;
-    float dy = 0.f;
-    if (yy < cy) dy = my - fmaf((float)(yy + 1), c, g.y0);
-    else if (yy > cy) dy = fmaf((float)yy, c, g.y0) - my;
-    dy = fmaxf(dy - margin, 0.f);
-    const float w2 = R2 - dy * dy;
-    if (w2 < 0.f) return make_int2(xa, xa - 1);
-    const float w = sqrtf(w2) + margin;
-    const int a = min(max(__float2int_rd((mx - w - g.x0) * g.inv_c), 0), W - 1);
-    const int b = min(max(__float2int_rd((mx + w - g.x0) * g.inv_c), 0), W - 1);
-    return make_int2(max(a, xa), min(b, xb));
-}
-
 // A2: the K nearest agents within R of agent `self` (in cell (cx, cy) of a
-// W x H grid placed by `geom` with cell size >= R / span, so that every
-// neighbour lies within `span` cells), ordered by (FP64 key, index) exactly
-// as the definition ranks them.  Of each row of the block only the cells
-// that reach the disk of radius R round the agent are scanned (clip_row).
+// W x H grid with cell size >= R / span, so that every neighbour lies within
+// `span` cells), ordered by (FP64 key, index) exactly as the definition
+// ranks them.
 //
 // Candidates are ranked by their FP32 squared distance packed with their
 // slot in the candidate source into one 64-bit key (the index is loaded only
@@ -227,9 +192,8 @@ __device__ __forceinline__ int2 clip_row(const CellGeom& g, int W, float mx, flo
 // rescanned with FP64 keys.  Candidates within kKeyRelErr of R^2 are admitted
 // by their FP64 key.  The list keeps KMAX + 2 >= K + 2 entries.
 template <int KMAX, class Src>
-__device__ __forceinline__ void select_neighbors(const Src& src, const CellGeom& geom, int cx, int cy, int W, int H,
-                                                 int self, float4 me, float R, int K, NbList<KMAX>& out, Tally& w,
-                                                 int span = 1) {
+__device__ __forceinline__ void select_neighbors(const Src& src, int cx, int cy, int W, int H, int self, float4 me,
+                                                 float R, int K, NbList<KMAX>& out, Tally& w, int span = 1) {
     constexpr int CAP = KMAX + 2;
     const float R2 = R * R;
     const float R2hi = R2 * (1.f + kKeyRelErr), R2lo = R2 * (1.f - kKeyRelErr);
@@ -238,42 +202,26 @@ __device__ __forceinline__ void select_neighbors(const Src& src, const CellGeom&
     const double xi = (double)me.x, yi = (double)me.y;
     const int xa = max(cx - span, 0), xb = min(cx + span, W - 1);
     const int ya = max(cy - span, 0), yb = min(cy + span, H - 1);
-    // clipping margin: 1e-3 of a cell plus a few units of 2^-24 of the
-    // coordinates' magnitude (the rounding of cell edges and of x - x0)
-    const float margin = 1e-3f / geom.inv_c + 1e-6f * (fabsf(geom.x0) + fabsf(geom.y0) + fabsf(me.x) + fabsf(me.y));
     TopK32<CAP> top;
     top.init();
     // the rows of the cell block are walked as one sequence (a warp then
     // iterates as often as its longest sequence, not its longest row per
     // row), and the next candidate is loaded while this one is ranked
     int yy = ya;
-    int2 cl = clip_row(geom, W, me.x, me.y, cy, yy, xa, xb, R2hi, margin);
-    int2 r = src.row(yy, cl.x, cl.y);
+    int2 r = src.row(yy, xa, xb);
     unsigned long long ncand = (unsigned long long)(r.y - r.x);
     while (r.x == r.y && yy < yb) {
-        ++yy;
-        cl = clip_row(geom, W, me.x, me.y, cy, yy, xa, xb, R2hi, margin);
-        r = src.row(yy, cl.x, cl.y);
+        r = src.row(++yy, xa, xb);
         ncand += (unsigned long long)(r.y - r.x);
     }
     int u = r.x, end = r.y;
     float4 nxt = u < end ? src.cand(u) : make_float4(0.f, 0.f, 0.f, 0.f);
-#if CROWD_SEL_BUF
-    // candidates below the list's current bound wait in a small buffer; the
-    // lanes of the warp insert theirs together once some lane's buffer is
-    // full, so that one pass of the insertion code serves all of them (the
-    // kept set is the same: the CAP smallest keys)
-    unsigned long long buf[CROWD_SEL_BUF];
-    int nbuf = 0;
-#endif
     while (u < end) {
         const float4 o = nxt;
         const int cu = u;
         if (++u == end && yy < yb) {
             do {
-                ++yy;
-                cl = clip_row(geom, W, me.x, me.y, cy, yy, xa, xb, R2hi, margin);
-                r = src.row(yy, cl.x, cl.y);
+                r = src.row(++yy, xa, xb);
                 ncand += (unsigned long long)(r.y - r.x);
             } while (r.x == r.y && yy < yb);
             u = r.x;
@@ -286,32 +234,9 @@ __device__ __forceinline__ void select_neighbors(const Src& src, const CellGeom&
             if (d2 == 0.f && src.cand_id(cu) == self) continue;
             if (d2 > R2lo && !(rank_key(xi, yi, o.x, o.y) < R2bits)) continue;
             ++w.pairs_in_range;
-            const unsigned long long x = ((unsigned long long)__float_as_uint(d2) << 32) | (unsigned)cu;
-#if CROWD_SEL_BUF
-            if (x < top.e[CAP - 1]) {
-#pragma unroll
-                for (int j = 0; j < CROWD_SEL_BUF; ++j)
-                    if (nbuf == j) buf[j] = x;
-                ++nbuf;
-            }
-#else
-            top.insert(x);
-#endif
+            top.insert(((unsigned long long)__float_as_uint(d2) << 32) | (unsigned)cu);
         }
-#if CROWD_SEL_BUF
-        if (__any_sync(__activemask(), nbuf == CROWD_SEL_BUF)) {
-#pragma unroll
-            for (int j = 0; j < CROWD_SEL_BUF; ++j)
-                if (j < nbuf) top.insert(buf[j]);
-            nbuf = 0;
-        }
-#endif
     }
-#if CROWD_SEL_BUF
-#pragma unroll
-    for (int j = 0; j < CROWD_SEL_BUF; ++j)
-        if (j < nbuf) top.insert(buf[j]);
-#endif
     w.candidates += ncand;
     const int cnt = top.cnt;
     // tie[s]: keys s and s + 1 are near-equal (s + 1 < cnt)

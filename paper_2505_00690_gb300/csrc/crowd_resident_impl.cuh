@@ -268,7 +268,7 @@ __device__ __forceinline__ bool agent_update(const ResidentArgs& a, const AgentP
     // A1/A2: K nearest within R, ranked by (FP64 key, index)
     NbList<KMAX> nb;
     const SmemSource src{S.spv, S.sid, S.cell, c.g.W};
-    select_neighbors<KMAX>(src, CellGeom{c.g.x0, c.g.y0, c.g.inv_c}, cell_coord(me.x, c.g.x0, c.g.inv_c, c.g.W),
+    select_neighbors<KMAX>(src, cell_coord(me.x, c.g.x0, c.g.inv_c, c.g.W),
                            cell_coord(me.y, c.g.y0, c.g.inv_c, c.g.H), c.g.W, c.g.H, i, me, a.R, a.K, nb, w,
                            a.cell_split);
     const int K = a.K;
@@ -306,7 +306,7 @@ __device__ __noinline__ void vehicle_update(const ResidentArgs& a, const Smem& S
     if (c.last && a.nbr_out) {
         NbList<KMAX> nb;
         const SmemSource src{S.spv, S.sid, S.cell, c.g.W};
-        select_neighbors<KMAX>(src, CellGeom{c.g.x0, c.g.y0, c.g.inv_c}, cell_coord(me.x, c.g.x0, c.g.inv_c, c.g.W),
+        select_neighbors<KMAX>(src, cell_coord(me.x, c.g.x0, c.g.inv_c, c.g.W),
                                cell_coord(me.y, c.g.y0, c.g.inv_c, c.g.H), c.g.W, c.g.H, i, me, a.R, a.K, nb, w,
                                a.cell_split);
         int* out = a.nbr_out + (size_t)(c.base + i) * a.K;
