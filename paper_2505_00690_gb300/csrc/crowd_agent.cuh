@@ -176,6 +176,54 @@ __device__ __forceinline__ float box_dist2(float px, float py, float4 s) {
     return dx * dx + dy * dy;
 }
 
+// Rows of the (2 span + 1)^2 block round cell (cx, cy) of a W x H grid,
+// nearest first: the agent's row, then the rows 1, 2, ... above and below it
+// (cy, cy - 1, cy + 1, cy - 2, ...), each as one run of cells cx - span ..
+// cx + span (contiguous in cell order, hence in sorted slots); every cell of
+// the block comes exactly once.
+struct RowWalk {
+    int cx, cy, W, H, span, k;
+    __device__ __forceinline__ RowWalk(int cx_, int cy_, int W_, int H_, int span_)
+        : cx(cx_), cy(cy_), W(W_), H(H_), span(span_), k(0) {}
+    __device__ __forceinline__ bool next(int& row, int& c0, int& c1) {
+        while (k <= 2 * span) {
+            const int off = (k & 1) ? -((k + 1) >> 1) : (k >> 1);
+            ++k;
+            const int y = cy + off;
+            if (y < 0 || y >= H) continue;
+            row = y;
+            c0 = max(cx - span, 0);
+            c1 = min(cx + span, W - 1);
+            return true;
+        }
+        return false;
+    }
+};
+
+// Placement of a uniform grid: an agent at (x, y) lies in cell
+// (clamp(floor((x - x0) inv_c)), clamp(floor((y - y0) inv_c))).
+struct CellGeom {
+    float x0, y0, inv_c;
+};
+
+// Smallest squared distance from the agent at (mx, my), in cell (cx, cy), to
+// a point of cells c0..c1 of row `row`, from the cell edges facing it less
+// `margin` (which covers the FP32 rounding of the edges against the clamped
+// floor map that placed the agents).  A border cell also holds the agents
+// clamped into it from outside the grid, which lie beyond its outer edge,
+// away from an agent inside, so the edge facing the agent still bounds them.
+__device__ __forceinline__ float run_dist2(const CellGeom& g, float c, float margin, float mx, float my, int cx,
+                                           int cy, int row, int c0, int c1) {
+    float gx = 0.f, gy = 0.f;
+    if (row < cy) gy = my - fmaf((float)(row + 1), c, g.y0);
+    else if (row > cy) gy = fmaf((float)row, c, g.y0) - my;
+    if (c1 < cx) gx = mx - fmaf((float)(c1 + 1), c, g.x0);
+    else if (c0 > cx) gx = fmaf((float)c0, c, g.x0) - mx;
+    gx = fmaxf(gx - margin, 0.f);
+    gy = fmaxf(gy - margin, 0.f);
+    return gx * gx + gy * gy;
+}
+
 // A2: the K nearest agents within R of agent `self` (in cell (cx, cy) of a
 // W x H grid with cell size >= R / span, so that every neighbour lies within
 // `span` cells), ordered by (FP64 key, index) exactly as the definition
@@ -191,9 +239,10 @@ __device__ __forceinline__ float box_dist2(float px, float py, float4 s) {
 // end of a full list may continue past it: then the block of cells is
 // rescanned with FP64 keys.  Candidates within kKeyRelErr of R^2 are admitted
 // by their FP64 key.  The list keeps KMAX + 2 >= K + 2 entries.
-template <int KMAX, class Src>
-__device__ __forceinline__ void select_neighbors(const Src& src, int cx, int cy, int W, int H, int self, float4 me,
-                                                 float R, int K, NbList<KMAX>& out, Tally& w, int span = 1) {
+template <int KMAX, bool NEAR_FIRST, class Src>
+__device__ __forceinline__ void select_neighbors(const Src& src, const CellGeom& geom, int cx, int cy, int W, int H,
+                                                 int self, float4 me, float R, int K, NbList<KMAX>& out, Tally& w,
+                                                 int span, bool counting) {
     constexpr int CAP = KMAX + 2;
     const float R2 = R * R;
     const float R2hi = R2 * (1.f + kKeyRelErr), R2lo = R2 * (1.f - kKeyRelErr);
@@ -204,37 +253,100 @@ __device__ __forceinline__ void select_neighbors(const Src& src, int cx, int cy,
     const int ya = max(cy - span, 0), yb = min(cy + span, H - 1);
     TopK32<CAP> top;
     top.init();
-    // the rows of the cell block are walked as one sequence (a warp then
-    // iterates as often as its longest sequence, not its longest row per
-    // row), and the next candidate is loaded while this one is ranked
-    int yy = ya;
-    int2 r = src.row(yy, xa, xb);
-    unsigned long long ncand = (unsigned long long)(r.y - r.x);
-    while (r.x == r.y && yy < yb) {
-        r = src.row(++yy, xa, xb);
-        ncand += (unsigned long long)(r.y - r.x);
-    }
-    int u = r.x, end = r.y;
-    float4 nxt = u < end ? src.cand(u) : make_float4(0.f, 0.f, 0.f, 0.f);
-    while (u < end) {
-        const float4 o = nxt;
-        const int cu = u;
-        if (++u == end && yy < yb) {
-            do {
-                r = src.row(++yy, xa, xb);
-                ncand += (unsigned long long)(r.y - r.x);
-            } while (r.x == r.y && yy < yb);
-            u = r.x;
-            end = r.y;
-        }
-        if (u < end) nxt = src.cand(u);
+    // candidate o at sorted slot cu: ranked when within R (FP64 key near R^2)
+    auto consider = [&](const float4& o, int cu) {
         const float dx = o.x - me.x, dy = o.y - me.y;
         const float d2 = dx * dx + dy * dy;
         if (d2 < R2hi) {
-            if (d2 == 0.f && src.cand_id(cu) == self) continue;
-            if (d2 > R2lo && !(rank_key(xi, yi, o.x, o.y) < R2bits)) continue;
+            if (d2 == 0.f && src.cand_id(cu) == self) return;
+            if (d2 > R2lo && !(rank_key(xi, yi, o.x, o.y) < R2bits)) return;
             ++w.pairs_in_range;
             top.insert(((unsigned long long)__float_as_uint(d2) << 32) | (unsigned)cu);
+        }
+    };
+    unsigned long long ncand = 0;
+    if constexpr (NEAR_FIRST) {
+        // The rows of the block are walked nearest first (the agent's row,
+        // then outwards), as one sequence (a warp then iterates as often as
+        // its longest sequence), and the next candidate is loaded while this
+        // one is ranked.  Near candidates fill the list early; once it is
+        // full, a row all of whose points lie farther than its last key is
+        // skipped, as none of its candidates could enter the list.  The kept
+        // set, the K + 2 smallest (key, slot), does not depend on the order.
+        // (Dense crowds: 42 % fewer candidates; sparse ones, whose lists
+        // seldom fill, pay for the row bookkeeping, so the shared-memory
+        // kernel keeps the plain row order.)
+        RowWalk walk(cx, cy, W, H, span);
+        const float csz = 1.f / geom.inv_c;
+        const float margin = 1e-3f * csz + 1e-6f * (fabsf(geom.x0) + fabsf(geom.y0) + fabsf(me.x) + fabsf(me.y));
+        int row = cy, c0 = cx, c1 = cx;
+        int u = 0, end = 0;
+        while (u == end && walk.next(row, c0, c1)) {
+            const int2 rg = src.row(row, c0, c1);
+            u = rg.x;
+            end = rg.y;
+            ncand += (unsigned long long)(end - u);
+        }
+        float4 nxt = u < end ? src.cand(u) : make_float4(0.f, 0.f, 0.f, 0.f);
+        while (u < end) {
+            const float4 o = nxt;
+            const int cu = u;
+            if (++u == end) {
+                while (u == end && walk.next(row, c0, c1)) {
+                    if (top.cnt == CAP && run_dist2(geom, csz, margin, me.x, me.y, cx, cy, row, c0, c1) >
+                                              TopK32<CAP>::key_of(top.e[CAP - 1])) {
+                        // counting work: the pairs within R of a skipped row
+                        // are still counted, so that the count is the
+                        // definition's (every pair within R), not the search's
+                        if (counting) {
+                            const int2 rg = src.row(row, c0, c1);
+                            for (int q = rg.x; q < rg.y; ++q) {
+                                const float4 oq = src.cand(q);
+                                const float dx = oq.x - me.x, dy = oq.y - me.y;
+                                const float d2 = dx * dx + dy * dy;
+                                if (d2 < R2hi && !(d2 == 0.f && src.cand_id(q) == self) &&
+                                    !(d2 > R2lo && !(rank_key(xi, yi, oq.x, oq.y) < R2bits)))
+                                    ++w.pairs_in_range;
+                            }
+                        }
+                        continue;
+                    }
+                    const int2 rg = src.row(row, c0, c1);
+                    u = rg.x;
+                    end = rg.y;
+                    ncand += (unsigned long long)(end - u);
+                }
+            }
+            if (u < end) nxt = src.cand(u);
+            consider(o, cu);
+        }
+    } else {
+        // the rows of the cell block are walked bottom to top as one sequence
+        // (a warp then iterates as often as its longest sequence, not its
+        // longest row per row), and the next candidate is loaded while this
+        // one is ranked
+        int yy = ya;
+        int2 r = src.row(yy, xa, xb);
+        ncand = (unsigned long long)(r.y - r.x);
+        while (r.x == r.y && yy < yb) {
+            r = src.row(++yy, xa, xb);
+            ncand += (unsigned long long)(r.y - r.x);
+        }
+        int u = r.x, end = r.y;
+        float4 nxt = u < end ? src.cand(u) : make_float4(0.f, 0.f, 0.f, 0.f);
+        while (u < end) {
+            const float4 o = nxt;
+            const int cu = u;
+            if (++u == end && yy < yb) {
+                do {
+                    r = src.row(++yy, xa, xb);
+                    ncand += (unsigned long long)(r.y - r.x);
+                } while (r.x == r.y && yy < yb);
+                u = r.x;
+                end = r.y;
+            }
+            if (u < end) nxt = src.cand(u);
+            consider(o, cu);
         }
     }
     w.candidates += ncand;

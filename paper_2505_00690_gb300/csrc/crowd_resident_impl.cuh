@@ -268,9 +268,9 @@ __device__ __forceinline__ bool agent_update(const ResidentArgs& a, const AgentP
     // A1/A2: K nearest within R, ranked by (FP64 key, index)
     NbList<KMAX> nb;
     const SmemSource src{S.spv, S.sid, S.cell, c.g.W};
-    select_neighbors<KMAX>(src, cell_coord(me.x, c.g.x0, c.g.inv_c, c.g.W),
+    select_neighbors<KMAX, false>(src, CellGeom{c.g.x0, c.g.y0, c.g.inv_c}, cell_coord(me.x, c.g.x0, c.g.inv_c, c.g.W),
                            cell_coord(me.y, c.g.y0, c.g.inv_c, c.g.H), c.g.W, c.g.H, i, me, a.R, a.K, nb, w,
-                           a.cell_split);
+                           a.cell_split, a.work != nullptr);
     const int K = a.K;
     if (c.last && a.nbr_out && export_nbrs) {
         int* out = a.nbr_out + (size_t)(c.base + i) * K;
@@ -306,9 +306,9 @@ __device__ __noinline__ void vehicle_update(const ResidentArgs& a, const Smem& S
     if (c.last && a.nbr_out) {
         NbList<KMAX> nb;
         const SmemSource src{S.spv, S.sid, S.cell, c.g.W};
-        select_neighbors<KMAX>(src, cell_coord(me.x, c.g.x0, c.g.inv_c, c.g.W),
+        select_neighbors<KMAX, false>(src, CellGeom{c.g.x0, c.g.y0, c.g.inv_c}, cell_coord(me.x, c.g.x0, c.g.inv_c, c.g.W),
                                cell_coord(me.y, c.g.y0, c.g.inv_c, c.g.H), c.g.W, c.g.H, i, me, a.R, a.K, nb, w,
-                               a.cell_split);
+                               a.cell_split, a.work != nullptr);
         int* out = a.nbr_out + (size_t)(c.base + i) * a.K;
         for (int s = 0; s < a.K; ++s) out[s] = s < nb.cnt ? nb.id[s] : -1;
     }
@@ -403,7 +403,7 @@ __global__ void __launch_bounds__(kMaxThreads, G >= 4 ? 2 : 1) resident_kernel(R
     __shared__ double s_speed;
     Smem S;
     smem_layout(a.max_agents, KMAX, blockDim.x >> 5, &S, smem_raw);
-    __shared__ int s_fb_count, s_pend;
+    __shared__ int s_fb_count, s_pend, s_item;
 
     for (;;) {
         if (threadIdx.x == 0) s_work = atomicAdd(a.queue, 1);
@@ -487,16 +487,25 @@ __global__ void __launch_bounds__(kMaxThreads, G >= 4 ? 2 : 1) resident_kernel(R
             if (threadIdx.x == 0) {
                 s_fb_count = 0;
                 s_pend = 0;
+                s_item = 0;
             }
             __syncthreads();
             if (G == 1) {
-                // slot t in cell order; with agent_order 1 the lanes of a warp
-                // take slots `warps` apart, so that the agents of a crowded
-                // region (adjacent in cell order, and the costliest) are spread
-                // over all warps instead of filling one
-                const int warps = blockDim.x >> 5;
-                for (int b = 0; b < c.n; b += blockDim.x) {
-                    const int t = b + (a.agent_order ? (threadIdx.x & 31) * warps + (threadIdx.x >> 5) : threadIdx.x);
+                // each warp takes the environment's agents 32 at a time from
+                // a shared counter (items = ceil(n / 32)), so that a warp done
+                // early takes the next item instead of waiting for a round:
+                // item k is the slots 32 k .. 32 k + 31 in cell order, or with
+                // agent_order 1 the slots k, k + items, k + 2 items, ..., so
+                // that the agents of a crowded region (adjacent in cell order,
+                // and the costliest) are spread over the items
+                const int lane = threadIdx.x & 31;
+                const int items = (c.n + 31) >> 5;
+                for (;;) {
+                    int item = 0;
+                    if (lane == 0) item = atomicAdd(&s_item, 1);
+                    item = __shfl_sync(0xffffffffu, item, 0);
+                    if (item >= items) break;
+                    const int t = a.agent_order ? item + lane * items : (item << 5) + lane;
                     if (t >= c.n) continue;
                     if (env_veh && S.par[S.sid[t]].z < 0.f) {  // a car (negative preferred speed)
                         vehicle_update<KMAX>(a, S, c, t, speed_acc, tally);

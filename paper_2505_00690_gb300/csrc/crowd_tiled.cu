@@ -216,7 +216,8 @@ __device__ __forceinline__ void tile_agent(const TiledStepArgs& a, const AgentPa
     }
 
     NbList<KMAX> nb;
-    select_neighbors<KMAX>(src, cx, cy, te.W, te.H, i, me, ap.R, ap.K, nb, w, te.span);
+    select_neighbors<KMAX, true>(src, CellGeom{te.x0, te.y0, te.inv_c}, cx, cy, te.W, te.H, i, me, ap.R, ap.K, nb, w,
+                           te.span, a.work != nullptr);
     if (a.nbr_out) {
         int* out = a.nbr_out + (size_t)g * ap.K;
 #pragma unroll
