@@ -463,7 +463,10 @@ def profile_case(which):
     full 1000-step rollout (for one-pass counters only); `tiled` = two single
     steps of one 20,000-agent dense-crowd environment (the second is
     captured); `dense` = two single steps of the 16-environment dense crowd
-    (the headline workload; the second step's update is captured)."""
+    (the headline workload; the second step's update is captured);
+    `dense_rollout` = the headline workload's timed form on a short rollout:
+    one warm single step, then one 20-step call (graph-replayed), every
+    launch of which a one-pass launch list can take."""
     from paper_2505_00690_gb300 import build as B
     from paper_2505_00690_gb300 import crowd as cw
     from paper_2505_00690_gb300 import scenes
@@ -486,6 +489,11 @@ def profile_case(which):
         cr = cw.Crowd(sc)
         cr.step(n_steps=1)
         cr.step(n_steps=1)
+    elif which == "dense_rollout":
+        sc = scenes.dense_crowd(0, steps=20)
+        cr = cw.Crowd(sc)
+        cr.step(n_steps=1)
+        cr.step(n_steps=20)
     else:
         sc = scenes.dense_crowd(0, n_envs=1, steps=4)
         cr = cw.Crowd(sc)
@@ -535,7 +543,7 @@ def main():
     ap.add_argument("--serve-seconds", type=float, default=10.0)
     ap.add_argument("--cpu-table", action="store_true",
                     help="time the FP64 oracle on every workload (1 and all host threads) and exit")
-    ap.add_argument("--profile-case", choices=["resident", "rollout", "tiled", "dense"], default=None,
+    ap.add_argument("--profile-case", choices=["resident", "rollout", "tiled", "dense", "dense_rollout"], default=None,
                     help="run a small case for an ncu capture and exit")
     args = ap.parse_args()
     if args.cpu_table:

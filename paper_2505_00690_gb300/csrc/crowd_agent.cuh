@@ -28,6 +28,8 @@ struct FbEntry {
     float vmax;
     float2 pref;
     float4 me;     // step-start state
+    int begin;     // line at which the 2D LP failed (lp_fallback's warm start), or -1
+    float2 vb;     // the 2D LP's last iterate
 };
 struct FbQueue {
     int* count;
@@ -36,12 +38,12 @@ struct FbQueue {
     Line* pool;      // cap x lmax lines
     bool in_place;   // a full queue sends the agent to the in-place fallback (else it runs again)
     __device__ __forceinline__ bool push(const Line* L, int n, int n_hard, float vmax, float2 pref, int agent,
-                                         float4 me) const {
+                                         float4 me, int begin, float2 vb) const {
         const int slot = atomicAdd(count, 1);
         if (slot >= cap) return false;
         Line* dst = pool + (size_t)slot * lmax;
         for (int k = 0; k < n; ++k) dst[k] = L[k];
-        entries[slot] = FbEntry{agent, n, n_hard, vmax, pref, me};
+        entries[slot] = FbEntry{agent, n, n_hard, vmax, pref, me, begin, vb};
         return true;
     }
 };
@@ -536,14 +538,18 @@ __device__ __forceinline__ float2 solve_velocity(const AgentParams& a, const Age
     const int nl = no + nb.cnt;
     int solves = 0, solve_lines = 0;
     float2 v;
-    const bool feasible = lp2(L, nl, pr.y, pref, v, solves, solve_lines) == nl;
+    const int fail = lp2(L, nl, pr.y, pref, v, solves, solve_lines);
+    const bool feasible = fail == nl;
     if (!feasible) {
-        if (fbq) queued = fbq->push(L, nl, no, pr.y, pref, i, me);
+        // the fallback starts where the 2D LP failed, from its last iterate,
+        // when every static line lies before that point
+        const int begin = fail >= no ? fail : -1;
+        if (fbq) queued = fbq->push(L, nl, no, pr.y, pref, i, me, begin, v);
         if (fbq && !queued && !fbq->in_place) {
             deferred = true;
         } else if (!queued) {
             Line scratch[KMAX + kMaxObstacleLines];
-            v = lp_fallback(L, nl, no, pr.y, pref, scratch);
+            v = lp_fallback(L, nl, no, pr.y, pref, scratch, begin, v);
         }
     }
     w.agent_lines += nb.cnt;

@@ -764,17 +764,35 @@ __device__ __forceinline__ bool lp_dir(const Line* S, int m, float vmax, float o
 // unique except when that subproblem's optimum is a whole interval, where
 // lp_dir takes the point closest to pref.  S is scratch for the subproblem
 // lines (at least n entries).
-__device__ __forceinline__ float2 lp_fallback(const Line* L, int n, int n_hard, float vmax, float2 pref, Line* S) {
+//
+// Warm start: when the 2D LP failed at line `begin` >= n_hard, its last
+// iterate `v_begin` satisfies every line before `begin` (the hard ones
+// among them), so the least maximal penetration, which is positive, is
+// found by the same increments started there with penetration bound 0 and
+// line `begin`: the lines before it cannot be penetrated more than 0 by
+// that point.  The optimum is the same; the increments over the lines the
+// 2D LP already satisfied are skipped.  begin < 0: start from the hard
+// lines' LP.
+__device__ __forceinline__ float2 lp_fallback(const Line* L, int n, int n_hard, float vmax, float2 pref, Line* S,
+                                              int begin = -1, float2 v_begin = float2{0.f, 0.f}) {
     float2 v;
-    int solves = 0, solve_lines = 0;
-    if (lp2(L, n_hard, vmax, pref, v, solves, solve_lines) < n_hard) {
-        n_hard = 0;
-        const float pl2 = fdot2(pref.x, pref.x, pref.y, pref.y);
-        const float k = pl2 > __fmul_rn(vmax, vmax) ? vmax * rsqrtf(pl2) : 1.f;
-        v = make_float2(pref.x * k, pref.y * k);
-    }
     float dist = -INFINITY;
-    for (int i = n_hard; i < n; ++i) {
+    int i0 = n_hard;
+    if (begin >= n_hard && begin < n) {
+        v = v_begin;
+        dist = 0.f;
+        i0 = begin;
+    } else {
+        int solves = 0, solve_lines = 0;
+        if (lp2(L, n_hard, vmax, pref, v, solves, solve_lines) < n_hard) {
+            n_hard = 0;
+            const float pl2 = fdot2(pref.x, pref.x, pref.y, pref.y);
+            const float k = pl2 > __fmul_rn(vmax, vmax) ? vmax * rsqrtf(pl2) : 1.f;
+            v = make_float2(pref.x * k, pref.y * k);
+        }
+        i0 = n_hard;
+    }
+    for (int i = i0; i < n; ++i) {
         const Line li = L[i];
         const float viol = -side_of(v.x, v.y, li.qx, li.qy, li.nx, li.ny);
         if (viol > dist) {
