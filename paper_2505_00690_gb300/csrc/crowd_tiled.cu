@@ -308,7 +308,7 @@ __global__ void __launch_bounds__(kUpdateThreads) tiled_update(TiledStepArgs a) 
     }
     __syncthreads();
 
-    const AgentParams ap{a.R, a.dt, a.tau, a.tau_o, a.robot_alpha, a.K, a.segs, a.err, a.seg_vd};
+    const AgentParams ap{a.R, a.dt, a.tau, a.tau_o, a.robot_alpha, a.K, a.segs, a.err, a.seg_vd, 1};
     Tally w;
     unsigned long long ca = 0, cs = 0;
     double speed = 0.0;
@@ -368,7 +368,7 @@ __device__ __forceinline__ double warp_sum(double v) {
 template <int KMAX>
 __global__ void __launch_bounds__(kQueueThreads, kQueueMinBlocks) tiled_update_queue(TiledStepArgs a) {
     const int lane = threadIdx.x & 31;
-    const AgentParams ap{a.R, a.dt, a.tau, a.tau_o, a.robot_alpha, a.K, a.segs, a.err, a.seg_vd};
+    const AgentParams ap{a.R, a.dt, a.tau, a.tau_o, a.robot_alpha, a.K, a.segs, a.err, a.seg_vd, 1};
     Tally w;
     for (;;) {
         int item = 0;
