@@ -101,12 +101,6 @@ struct AgentParams {
     const float4* segs;  // segments of all environments
     int* err;            // device error word
     int seg_vd;          // 1: velocity-dependent segment half-planes (obstacle_line_vd)
-    // 1: an infeasible LP's fallback starts where the LP failed (lp_fallback's
-    // warm start).  The persistent tiled update takes it (16 x 20,000 crowd
-    // 9 % faster, uneven batch on that path 9 %); the shared-memory kernel,
-    // whose step waits for its slowest agent, ran the uneven batch 23 %
-    // slower with it (same results), so it starts from the static lines.
-    int fb_warm;
 };
 
 // Velocity-dependent mode: segment s gets no line when an earlier segment
@@ -472,7 +466,12 @@ struct ListedSegments {
 // `deferred` is set instead and the caller runs the agent again in a later
 // round (so that every fallback of a queued run takes the same cooperative
 // path, whatever the thread order).  Without a queue the fallback runs here.
-template <int KMAX, class Agents, class SegList>
+// WARM: an infeasible LP's fallback starts where the LP failed (lp_fallback's
+// warm start).  The persistent tiled update takes it (16 x 20,000 crowd 9 %
+// faster, the uneven batch on that path 9 %); the shared-memory kernel, whose
+// step waits for its slowest agent, ran the uneven batch 23 % slower with it
+// (same results) and is compiled without it.
+template <int KMAX, bool WARM, class Agents, class SegList>
 __device__ __forceinline__ float2 solve_velocity(const AgentParams& a, const Agents& ag, int i, int robot, float4 me,
                                                  float4 pr, float2 gl, int seg0, const SegList& sl,
                                                  const NbList<KMAX>& nb, Tally& w, const FbQueue* fbq,
@@ -549,7 +548,7 @@ __device__ __forceinline__ float2 solve_velocity(const AgentParams& a, const Age
     if (!feasible) {
         // the fallback starts where the 2D LP failed, from its last iterate,
         // when every static line lies before that point
-        const int begin = (a.fb_warm && fail >= no) ? fail : -1;
+        const int begin = (WARM && fail >= no) ? fail : -1;
         if (fbq) queued = fbq->push(L, nl, no, pr.y, pref, i, me, begin, v);
         if (fbq && !queued && !fbq->in_place) {
             deferred = true;

@@ -287,7 +287,7 @@ __device__ __forceinline__ bool agent_update(const ResidentArgs& a, const AgentP
         return false;
     }
     bool queued, deferred;
-    const float2 v = solve_velocity<KMAX>(ap, SmemAgents{S.pv, S.par}, i, c.robot, me, pr, S.goal[i], c.seg0,
+    const float2 v = solve_velocity<KMAX, false>(ap, SmemAgents{S.pv, S.par}, i, c.robot, me, pr, S.goal[i], c.seg0,
                                           cell_segments(a, c, me), nb, w, a.coop_fallback ? &fbq : nullptr, queued,
                                           deferred);
     if (!queued && !deferred) integrate(a, S, c, i, me, pr.x, v, speed_acc);
@@ -439,7 +439,7 @@ __global__ void __launch_bounds__(kMaxThreads, G >= 4 ? 2 : 1) resident_kernel(R
         // cars are looked for only in environments that have some (a test per
         // agent in the others cost the dense crowd a third of its time)
         const bool env_veh = a.veh.n > 0 && a.veh.start[c.e + 1] > a.veh.start[c.e];
-        const AgentParams ap{a.R, a.dt, a.tau, a.tau_o, a.robot_alpha, a.K, a.segs, a.err, a.seg_vd, 0};
+        const AgentParams ap{a.R, a.dt, a.tau, a.tau_o, a.robot_alpha, a.K, a.segs, a.err, a.seg_vd};
         // the queue capacity depends on this environment alone, so that its
         // results do not depend on the batch it runs in
         const FbQueue fbq{&s_fb_count, min(S.fb_cap, fb_capacity(c.n)), S.lmax, S.fb, S.fb_lines,

@@ -231,7 +231,7 @@ __device__ __forceinline__ void tile_agent(const TiledStepArgs& a, const AgentPa
         // segment candidates: the cell's precomputed list
         const int s0 = a.seg_cell_start[te.co + k], s1 = a.seg_cell_start[te.co + k + 1];
         bool queued, deferred;
-        v = solve_velocity<KMAX>(ap, GlobalAgents{a.state_in + te.base, a.par + te.base}, i, te.robot, me, pr,
+        v = solve_velocity<KMAX, true>(ap, GlobalAgents{a.state_in + te.base, a.par + te.base}, i, te.robot, me, pr,
                                  __ldg(&a.goal[g]), te.seg0, ListedSegments{a.seg_cell_ids + s0, s1 - s0}, nb, w,
                                  nullptr, queued, deferred);
     }
@@ -308,7 +308,7 @@ __global__ void __launch_bounds__(kUpdateThreads) tiled_update(TiledStepArgs a) 
     }
     __syncthreads();
 
-    const AgentParams ap{a.R, a.dt, a.tau, a.tau_o, a.robot_alpha, a.K, a.segs, a.err, a.seg_vd, 1};
+    const AgentParams ap{a.R, a.dt, a.tau, a.tau_o, a.robot_alpha, a.K, a.segs, a.err, a.seg_vd};
     Tally w;
     unsigned long long ca = 0, cs = 0;
     double speed = 0.0;
@@ -368,7 +368,7 @@ __device__ __forceinline__ double warp_sum(double v) {
 template <int KMAX>
 __global__ void __launch_bounds__(kQueueThreads, kQueueMinBlocks) tiled_update_queue(TiledStepArgs a) {
     const int lane = threadIdx.x & 31;
-    const AgentParams ap{a.R, a.dt, a.tau, a.tau_o, a.robot_alpha, a.K, a.segs, a.err, a.seg_vd, 1};
+    const AgentParams ap{a.R, a.dt, a.tau, a.tau_o, a.robot_alpha, a.K, a.segs, a.err, a.seg_vd};
     Tally w;
     for (;;) {
         int item = 0;
