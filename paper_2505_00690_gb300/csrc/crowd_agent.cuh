@@ -28,8 +28,6 @@ struct FbEntry {
     float vmax;
     float2 pref;
     float4 me;     // step-start state
-    int begin;     // line at which the 2D LP failed (lp_fallback's warm start), or -1
-    float2 vb;     // the 2D LP's last iterate
 };
 struct FbQueue {
     int* count;
@@ -38,12 +36,12 @@ struct FbQueue {
     Line* pool;      // cap x lmax lines
     bool in_place;   // a full queue sends the agent to the in-place fallback (else it runs again)
     __device__ __forceinline__ bool push(const Line* L, int n, int n_hard, float vmax, float2 pref, int agent,
-                                         float4 me, int begin, float2 vb) const {
+                                         float4 me) const {
         const int slot = atomicAdd(count, 1);
         if (slot >= cap) return false;
         Line* dst = pool + (size_t)slot * lmax;
         for (int k = 0; k < n; ++k) dst[k] = L[k];
-        entries[slot] = FbEntry{agent, n, n_hard, vmax, pref, me, begin, vb};
+        entries[slot] = FbEntry{agent, n, n_hard, vmax, pref, me};
         return true;
     }
 };
@@ -546,15 +544,18 @@ __device__ __forceinline__ float2 solve_velocity(const AgentParams& a, const Age
     const int fail = lp2(L, nl, pr.y, pref, v, solves, solve_lines);
     const bool feasible = fail == nl;
     if (!feasible) {
-        // the fallback starts where the 2D LP failed, from its last iterate,
-        // when every static line lies before that point
-        const int begin = (WARM && fail >= no) ? fail : -1;
-        if (fbq) queued = fbq->push(L, nl, no, pr.y, pref, i, me, begin, v);
+        if (fbq) queued = fbq->push(L, nl, no, pr.y, pref, i, me);
         if (fbq && !queued && !fbq->in_place) {
             deferred = true;
         } else if (!queued) {
             Line scratch[KMAX + kMaxObstacleLines];
-            v = lp_fallback(L, nl, no, pr.y, pref, scratch, begin, v);
+            if constexpr (WARM) {
+                // the fallback starts where the 2D LP failed, from its last
+                // iterate, when every static line lies before that point
+                v = lp_fallback(L, nl, no, pr.y, pref, scratch, fail >= no ? fail : -1, v);
+            } else {
+                v = lp_fallback(L, nl, no, pr.y, pref, scratch);
+            }
         }
     }
     w.agent_lines += nb.cnt;

@@ -542,8 +542,7 @@ __global__ void __launch_bounds__(kMaxThreads, G >= 4 ? 2 : 1) resident_kernel(R
                 if (q < min(s_fb_count, fbq.cap)) {
                     const FbEntry f = S.fb[q];
                     Line scratch[KMAX + kMaxObstacleLines];
-                    const float2 v = lp_fallback(S.fb_lines + (size_t)q * S.lmax, f.n, f.n_hard, f.vmax, f.pref, scratch,
-                                                 f.begin, f.vb);
+                    const float2 v = lp_fallback(S.fb_lines + (size_t)q * S.lmax, f.n, f.n_hard, f.vmax, f.pref, scratch);
                     integrate(a, S, c, f.agent, f.me, S.par[f.agent].x, v, speed_acc);
                 }
                 __syncthreads();
