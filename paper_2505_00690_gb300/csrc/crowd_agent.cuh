@@ -552,7 +552,7 @@ __device__ __forceinline__ float2 solve_velocity(const AgentParams& a, const Age
             if constexpr (WARM) {
                 // the fallback starts where the 2D LP failed, from its last
                 // iterate, when every static line lies before that point
-                v = lp_fallback(L, nl, no, pr.y, pref, scratch, fail >= no ? fail : -1, v);
+                v = lp_fallback_warm(L, nl, no, pr.y, pref, scratch, fail >= no ? fail : -1, v);
             } else {
                 v = lp_fallback(L, nl, no, pr.y, pref, scratch);
             }

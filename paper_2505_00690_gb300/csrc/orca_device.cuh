@@ -765,33 +765,10 @@ __device__ __forceinline__ bool lp_dir(const Line* S, int m, float vmax, float o
 // lp_dir takes the point closest to pref.  S is scratch for the subproblem
 // lines (at least n entries).
 //
-// Warm start: when the 2D LP failed at line `begin` >= n_hard, its last
-// iterate `v_begin` satisfies every line before `begin` (the hard ones
-// among them), so the least maximal penetration, which is positive, is
-// found by the same increments started there with penetration bound 0 and
-// line `begin`: the lines before it cannot be penetrated more than 0 by
-// that point.  The optimum is the same; the increments over the lines the
-// 2D LP already satisfied are skipped.  begin < 0: start from the hard
-// lines' LP.
-__device__ __forceinline__ float2 lp_fallback(const Line* L, int n, int n_hard, float vmax, float2 pref, Line* S,
-                                              int begin = -1, float2 v_begin = float2{0.f, 0.f}) {
-    float2 v;
-    float dist = -INFINITY;
-    int i0 = n_hard;
-    if (begin >= n_hard && begin < n) {
-        v = v_begin;
-        dist = 0.f;
-        i0 = begin;
-    } else {
-        int solves = 0, solve_lines = 0;
-        if (lp2(L, n_hard, vmax, pref, v, solves, solve_lines) < n_hard) {
-            n_hard = 0;
-            const float pl2 = fdot2(pref.x, pref.x, pref.y, pref.y);
-            const float k = pl2 > __fmul_rn(vmax, vmax) ? vmax * rsqrtf(pl2) : 1.f;
-            v = make_float2(pref.x * k, pref.y * k);
-        }
-        i0 = n_hard;
-    }
+// The increments from line i0 on, from point v with penetration bound dist
+// (shared by both starts below).
+__device__ __forceinline__ float2 fallback_increments(const Line* L, int n, int n_hard, float vmax, float2 pref,
+                                                      Line* S, float2 v, float dist, int i0) {
     for (int i = i0; i < n; ++i) {
         const Line li = L[i];
         const float viol = -side_of(v.x, v.y, li.qx, li.qy, li.nx, li.ny);
@@ -816,6 +793,33 @@ __device__ __forceinline__ float2 lp_fallback(const Line* L, int n, int n_hard, 
         }
     }
     return v;
+}
+
+// Cold start: from the hard lines' LP (all lines soft when it is empty),
+// penetration bound -infinity, first agent line.
+__device__ __forceinline__ float2 lp_fallback(const Line* L, int n, int n_hard, float vmax, float2 pref, Line* S) {
+    float2 v;
+    int solves = 0, solve_lines = 0;
+    if (lp2(L, n_hard, vmax, pref, v, solves, solve_lines) < n_hard) {
+        n_hard = 0;
+        const float pl2 = fdot2(pref.x, pref.x, pref.y, pref.y);
+        const float k = pl2 > __fmul_rn(vmax, vmax) ? vmax * rsqrtf(pl2) : 1.f;
+        v = make_float2(pref.x * k, pref.y * k);
+    }
+    return fallback_increments(L, n, n_hard, vmax, pref, S, v, -INFINITY, n_hard);
+}
+
+// Warm start: when the 2D LP failed at line `begin` >= n_hard, its last
+// iterate `v_begin` satisfies every line before `begin` (the hard ones
+// among them), so the least maximal penetration, which is positive, is
+// found by the same increments started there with penetration bound 0 and
+// line `begin`: the lines before it cannot be penetrated more than 0 by
+// that point.  The optimum is the same; the increments over the lines the
+// 2D LP already satisfied are skipped.  Otherwise the cold start.
+__device__ __forceinline__ float2 lp_fallback_warm(const Line* L, int n, int n_hard, float vmax, float2 pref,
+                                                   Line* S, int begin, float2 v_begin) {
+    if (begin >= n_hard && begin < n) return fallback_increments(L, n, n_hard, vmax, pref, S, v_begin, 0.f, begin);
+    return lp_fallback(L, n, n_hard, vmax, pref, S);
 }
 
 // ---------------------------------------------------------------- A5, warp-cooperative ----
