@@ -46,9 +46,10 @@ WORKLOAD = ("dense_crowd: 16 envs x 20,000 pedestrians (2 per m^2 in 100x100 m, 
             "R 3 m, 500-step rollout, dt 0.1")
 ROLLOUT = 500
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch of the update
-# kernel on this workload (ncu, one pass, `bench.py --profile-case dense`),
-# or None when the kernel has changed since the counters were taken
-UPDATE_DRAM_BYTES = None
+# kernel on this workload (ncu, one pass, `bench.py --profile-case dense`:
+# the second step of the rollout, 26,551,552 + 26,931,200 bytes), or None
+# when the kernel has changed since the counters were taken
+UPDATE_DRAM_BYTES = 53_482_752
 FP32_LANES_PER_SM = 128
 N_SMS = 152
 SERVE_RATES = (200.0, 400.0, 800.0, 1600.0)
