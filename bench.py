@@ -467,7 +467,9 @@ def profile_case(which):
     (the headline workload; the second step's update is captured);
     `dense_rollout` = the headline workload's timed form on a short rollout:
     one warm single step, then one 20-step call (graph-replayed), every
-    launch of which a one-pass launch list can take."""
+    launch of which a one-pass launch list can take; `dense_jam` = the
+    headline workload's jammed phase: a 300-step call, then two single steps
+    (capture the last update, the 302nd)."""
     from paper_2505_00690_gb300 import build as B
     from paper_2505_00690_gb300 import crowd as cw
     from paper_2505_00690_gb300 import scenes
@@ -488,6 +490,12 @@ def profile_case(which):
     elif which == "dense":
         sc = scenes.dense_crowd(0, steps=4)
         cr = cw.Crowd(sc)
+        cr.step(n_steps=1)
+        cr.step(n_steps=1)
+    elif which == "dense_jam":
+        sc = scenes.dense_crowd(0, steps=300)
+        cr = cw.Crowd(sc)
+        cr.step(n_steps=300)
         cr.step(n_steps=1)
         cr.step(n_steps=1)
     elif which == "dense_rollout":
@@ -544,7 +552,7 @@ def main():
     ap.add_argument("--serve-seconds", type=float, default=10.0)
     ap.add_argument("--cpu-table", action="store_true",
                     help="time the FP64 oracle on every workload (1 and all host threads) and exit")
-    ap.add_argument("--profile-case", choices=["resident", "rollout", "tiled", "dense", "dense_rollout"], default=None,
+    ap.add_argument("--profile-case", choices=["resident", "rollout", "tiled", "dense", "dense_rollout", "dense_jam"], default=None,
                     help="run a small case for an ncu capture and exit")
     args = ap.parse_args()
     if args.cpu_table:
