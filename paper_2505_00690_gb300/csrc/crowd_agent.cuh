@@ -14,6 +14,8 @@
 
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "crowd_internal.h"
 #include "orca_device.cuh"
 #include "philox.cuh"
@@ -251,7 +253,11 @@ __device__ __forceinline__ void select_neighbors(const Src& src, const CellGeom&
     const double xi = (double)me.x, yi = (double)me.y;
     const int xa = max(cx - span, 0), xb = min(cx + span, W - 1);
     const int ya = max(cy - span, 0), yb = min(cy + span, H - 1);
-    TopK32<CAP> top;
+    // the tiled path's list splits keys and slots (fewer integer operations
+    // per insertion); the shared-memory kernel keeps the packed 64-bit list
+    // (its code is sensitive to register allocation)
+    using TopList = typename std::conditional<NEAR_FIRST, TopKSplit<CAP>, TopK32<CAP>>::type;
+    TopList top;
     top.init();
     // candidate o at sorted slot cu: ranked when within R (FP64 key near R^2)
     auto consider = [&](const float4& o, int cu) {
@@ -261,7 +267,7 @@ __device__ __forceinline__ void select_neighbors(const Src& src, const CellGeom&
             if (d2 == 0.f && src.cand_id(cu) == self) return;
             if (d2 > R2lo && !(rank_key(xi, yi, o.x, o.y) < R2bits)) return;
             ++w.pairs_in_range;
-            top.insert(((unsigned long long)__float_as_uint(d2) << 32) | (unsigned)cu);
+            top.put(d2, cu);
         }
     };
     unsigned long long ncand = 0;
@@ -293,8 +299,8 @@ __device__ __forceinline__ void select_neighbors(const Src& src, const CellGeom&
             const int cu = u;
             if (++u == end) {
                 while (u == end && walk.next(row, c0, c1)) {
-                    if (top.cnt == CAP && run_dist2(geom, csz, margin, me.x, me.y, cx, cy, row, c0, c1) >
-                                              TopK32<CAP>::key_of(top.e[CAP - 1])) {
+                    if (top.cnt == CAP &&
+                        run_dist2(geom, csz, margin, me.x, me.y, cx, cy, row, c0, c1) > top.key(CAP - 1)) {
                         // counting work: the pairs within R of a skipped row
                         // are still counted, so that the count is the
                         // definition's (every pair within R), not the search's
@@ -357,7 +363,7 @@ __device__ __forceinline__ void select_neighbors(const Src& src, const CellGeom&
 #pragma unroll
     for (int s = 0; s + 1 < CAP; ++s) {
         if (s + 1 < cnt && s < K) {
-            const float ka = TopK32<CAP>::key_of(top.e[s]), kb = TopK32<CAP>::key_of(top.e[s + 1]);
+            const float ka = top.key(s), kb = top.key(s + 1);
             if (kb - ka <= kKeyRelErr * kb) {
                 tie |= 1u << s;
                 any_tie = true;
@@ -367,7 +373,7 @@ __device__ __forceinline__ void select_neighbors(const Src& src, const CellGeom&
     if (!any_tie) {
         out.cnt = min(cnt, K);
 #pragma unroll
-        for (int s = 0; s < KMAX; ++s) out.id[s] = s < out.cnt ? src.cand_id((int)(unsigned)top.e[s]) : -1;
+        for (int s = 0; s < KMAX; ++s) out.id[s] = s < out.cnt ? src.cand_id(top.slot(s)) : -1;
         return;
     }
     // extend the run through position K - 1 to its end
@@ -376,7 +382,7 @@ __device__ __forceinline__ void select_neighbors(const Src& src, const CellGeom&
 #pragma unroll
         for (int s = 0; s + 1 < CAP; ++s) {
             if (s >= e && s + 1 < cnt && s + 1 == e + 1) {
-                const float ka = TopK32<CAP>::key_of(top.e[s]), kb = TopK32<CAP>::key_of(top.e[s + 1]);
+                const float ka = top.key(s), kb = top.key(s + 1);
                 if (kb - ka <= kKeyRelErr * kb) {
                     tie |= 1u << s;
                     e = s + 1;
@@ -412,7 +418,7 @@ __device__ __forceinline__ void select_neighbors(const Src& src, const CellGeom&
         kk[s] = 0ull;
         id[s] = -1;
         if (s <= e) {
-            const int u = (int)(unsigned)top.e[s];
+            const int u = top.slot(s);
             id[s] = src.cand_id(u);
             const bool member = ((tie >> s) & 1u) || (s > 0 && ((tie >> (s - 1)) & 1u));
             if (member) {

@@ -127,6 +127,51 @@ struct TopK32 {
         cnt = cnt < CAP ? cnt + 1 : CAP;
     }
     __device__ __forceinline__ static float key_of(unsigned long long x) { return __uint_as_float((unsigned)(x >> 32)); }
+    __device__ __forceinline__ void put(float d2, int slot) {
+        insert(((unsigned long long)__float_as_uint(d2) << 32) | (unsigned)slot);
+    }
+    __device__ __forceinline__ float key(int s) const { return key_of(e[s]); }
+    __device__ __forceinline__ int slot(int s) const { return (int)(unsigned)e[s]; }
+};
+
+// The same list with the FP32 keys and the candidate slots in two 32-bit
+// arrays: one 32-bit compare and two selects per word and entry instead of
+// a 64-bit compare and four selects (the insertion network is the update's
+// busiest integer work).  Equal keys keep their order of insertion, and a
+// key equal to the last one is not taken: exactly equal FP32 keys are near
+// ties, which the caller ranks again by (FP64 key, index), so the kept
+// neighbours are the same.
+template <int CAP>
+struct TopKSplit {
+    unsigned k[CAP];
+    int u[CAP];
+    int cnt;
+
+    __device__ __forceinline__ void init() {
+        cnt = 0;
+#pragma unroll
+        for (int s = 0; s < CAP; ++s) {
+            k[s] = 0xffffffffu;
+            u[s] = 0;
+        }
+    }
+    __device__ __forceinline__ void put(float d2, int slot) {
+        const unsigned x = __float_as_uint(d2);
+        if (x >= k[CAP - 1]) return;
+        bool gt[CAP];
+#pragma unroll
+        for (int s = 0; s < CAP; ++s) gt[s] = k[s] > x;
+#pragma unroll
+        for (int s = CAP - 1; s >= 1; --s) {
+            k[s] = gt[s - 1] ? k[s - 1] : (gt[s] ? x : k[s]);
+            u[s] = gt[s - 1] ? u[s - 1] : (gt[s] ? slot : u[s]);
+        }
+        k[0] = gt[0] ? x : k[0];
+        u[0] = gt[0] ? slot : u[0];
+        cnt = cnt < CAP ? cnt + 1 : CAP;
+    }
+    __device__ __forceinline__ float key(int s) const { return __uint_as_float(k[s]); }
+    __device__ __forceinline__ int slot(int s) const { return u[s]; }
 };
 
 // Relative error bound of the FP32 squared distance against the FP64
