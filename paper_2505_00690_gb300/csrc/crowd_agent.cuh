@@ -240,15 +240,12 @@ __device__ __forceinline__ float run_dist2(const CellGeom& g, float c, float mar
 // (FP64 key, index), computed for their members only.  A run that reaches the
 // end of a full list may continue past it: then the block of cells is
 // rescanned with FP64 keys.  Candidates within kKeyRelErr of R^2 are admitted
-// by their FP64 key.  The list keeps KMAX + 2 >= K + 2 entries, on the
-// tiled path KMAX + 1 >= K + 1 (one entry past the K-th is all the near-tie
-// test needs; a run reaching it then always takes the rescan, which the extra
-// entry saved only when keys K - 1 and K were near-equal but K and K + 1 not).
+// by their FP64 key.  The list keeps KMAX + 2 >= K + 2 entries.
 template <int KMAX, bool NEAR_FIRST, class Src>
 __device__ __forceinline__ void select_neighbors(const Src& src, const CellGeom& geom, int cx, int cy, int W, int H,
                                                  int self, float4 me, float R, int K, NbList<KMAX>& out, Tally& w,
                                                  int span, bool counting) {
-    constexpr int CAP = KMAX + (NEAR_FIRST ? 1 : 2);
+    constexpr int CAP = KMAX + 2;
     const float R2 = R * R;
     const float R2hi = R2 * (1.f + kKeyRelErr), R2lo = R2 * (1.f - kKeyRelErr);
     const double Rd = (double)R;
