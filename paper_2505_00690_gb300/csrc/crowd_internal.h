@@ -177,11 +177,11 @@ constexpr int kTiledUpdateThreads = 256;
 constexpr int kQueueThreads = 128;
 constexpr int kQueueItem = 32;
 // CTAs of the persistent update per SM the compiler budgets registers for
-// (65,536 / (5 x 128) = 102 a thread): 20 warps per SM ran the
-// 16 x 20,000 crowd 13 % faster than 16 warps at 128 registers, and 24 or
-// 32 warps (80 / 64 registers, more spills) no faster
+// (65,536 / (6 x 128) = 85, 80 a thread): on the 500-step 16 x 20,000 crowd
+// 6 CTAs (24 warps per SM) ran 263.9 ms, 5 CTAs (96 registers) 268.8 ms,
+// 4 (128 registers) slower still, 7 and 8 (more spills) 276.5 ms
 #ifndef CROWD_QUEUE_MINB
-#define CROWD_QUEUE_MINB 5
+#define CROWD_QUEUE_MINB 6
 #endif
 constexpr int kQueueMinBlocks = CROWD_QUEUE_MINB;
 // Cells of R / 2 are used when the tiled agents of a handle number at least
