@@ -47,9 +47,9 @@ WORKLOAD = ("dense_crowd: 16 envs x 20,000 pedestrians (2 per m^2 in 100x100 m, 
 ROLLOUT = 500
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch of the update
 # kernel on this workload (ncu, one pass, `bench.py --profile-case dense`:
-# the second step of the rollout, 26,551,552 + 26,931,200 bytes), or None
+# the second step of the rollout, 34,816,768 + 88,393,728 bytes), or None
 # when the kernel has changed since the counters were taken
-UPDATE_DRAM_BYTES = 53_482_752
+UPDATE_DRAM_BYTES = 123_210_496
 FP32_LANES_PER_SM = 128
 N_SMS = 152
 SERVE_RATES = (200.0, 400.0, 800.0, 1600.0)
