@@ -229,10 +229,10 @@ __device__ __forceinline__ float run_dist2(const CellGeom& g, float c, float mar
 // `span` cells), ordered by (FP64 key, index) exactly as the definition
 // ranks them.
 //
-// Candidates are ranked by their FP32 squared distance packed with their
-// slot in the candidate source into one 64-bit key (the index is loaded only
-// for the K kept, and for candidates at distance 0, which may be the agent
-// itself).  FP32 and FP64 keys further apart than kKeyRelErr order alike, so
+// Candidates are ranked by their FP32 squared distance, kept with their slot
+// in the candidate source (TopKSplit: the index is loaded only for the K
+// kept, and for candidates at distance 0, which may be the agent itself).
+// FP32 and FP64 keys further apart than kKeyRelErr order alike, so
 // the FP32 order is exact except inside runs of consecutive keys closer than
 // that ("near ties"); such runs among the first K + 1 are re-sorted by
 // (FP64 key, index), computed for their members only.  A run that reaches the
