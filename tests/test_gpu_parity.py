@@ -151,10 +151,15 @@ def _ragged_scene(sizes):
     return scenes._pack("ragged", envs)
 
 
+@pytest.mark.parametrize("tiled", [False, True])
 @pytest.mark.parametrize("sizes", [[1], [0, 5, 0], [31, 32, 33], [63, 64, 65, 1], [511, 512, 513]])
-def test_ragged_sizes(sizes):
+def test_ragged_sizes(sizes, tiled):
+    """Environments of 0, 1 and 2^k +- 1 agents, on the shared-memory kernel
+    and forced onto the tiled path (its 32-agent work items then end ragged)."""
+    from paper_2505_00690_gb300 import crowd as cw
+
     sc = _ragged_scene(sizes)
-    worst, mism, fb = teacher_forced(sc, 20)
+    worst, mism, fb = teacher_forced(sc, 20, flags=cw.CROWD_FLAG_FORCE_TILED if tiled else 0)
     assert mism == 0 and worst <= VEL_TOL
 
 
@@ -165,16 +170,42 @@ def test_largest_environment():
     assert mism == 0 and worst <= VEL_TOL
 
 
-def test_degenerate_geometry():
-    """Coincident agents, an agent exactly on a segment, K = 0 and K = 32."""
+@pytest.mark.parametrize("tiled", [False, True])
+def test_degenerate_geometry(tiled):
+    """Coincident agents, an agent exactly on a segment, K = 0 and K = 32, on
+    both paths (the tiled one ranks candidates with its nearest-row-first
+    walk)."""
+    from paper_2505_00690_gb300 import crowd as cw
+
     pos = [[0, 0], [0, 0], [3, 0], [3, 1e-7], [6, 1]]
     vel = [[0.5, 0], [0, 0], [0, 0], [0, 0], [0, 0.5]]
     goal = [[5, 5], [-5, -5], [3, 5], [3, -5], [6, 5]]
     seg = [(5, 1, 7, 1)]  # agent 4 sits on it
     for K in (0, 4, 32):
         sc = one_env(pos, vel, goal, 0.3, 1.2, segs=seg, K=K)
-        worst, mism, fb = teacher_forced(sc, 10)
+        worst, mism, fb = teacher_forced(sc, 10, flags=cw.CROWD_FLAG_FORCE_TILED if tiled else 0)
         assert mism == 0 and worst <= VEL_TOL, (K, worst)
+
+
+@pytest.mark.parametrize("tiled", [False, True])
+@pytest.mark.parametrize("K", [10, 16])
+def test_lattice_exact_ties(tiled, K):
+    """Agents on an exact 1 m lattice with R = 3 m: squared distances are
+    exact small integers, so whole rings of neighbours tie exactly (4 at 1,
+    4 at 2, 4 at 4, 8 at 5, 4 at 8 m^2), K = 10 and 16 fall inside a tied
+    ring (ranked by index), and the lattice points at exactly 3 m sit on the
+    R^2 boundary (excluded: the key must be below R^2)."""
+    from paper_2505_00690_gb300 import crowd as cw
+
+    rng = np.random.default_rng(11)
+    g = np.arange(14, dtype=np.float64) + 0.5
+    pos = np.array([[x, y] for y in g for x in g])
+    perm = rng.permutation(len(pos))  # indices not in lattice order
+    pos = pos[perm]
+    goal = rng.uniform(0, 14, pos.shape)
+    sc = one_env(pos, np.zeros_like(pos), goal, 0.3, 1.2, R=3.0, K=K)
+    worst, mism, fb = teacher_forced(sc, 2, flags=cw.CROWD_FLAG_FORCE_TILED if tiled else 0)
+    assert mism == 0 and worst <= VEL_TOL
 
 
 def test_robot_agent_follows_command():
