@@ -126,13 +126,17 @@ def test_uneven_polygons_teacher_forced():
     assert worst <= VEL_TOL, worst
 
 
-def test_dense_cluster_with_fallbacks():
-    """A jammed ring walking to the opposite side: many infeasible LPs."""
+@pytest.mark.parametrize("tiled", [False, True])
+def test_dense_cluster_with_fallbacks(tiled):
+    """A jammed ring walking to the opposite side: many infeasible LPs (on the
+    tiled path their fallback starts from the failed LP's iterate)."""
+    from paper_2505_00690_gb300 import crowd as cw
+
     n = 48
     ang = np.linspace(0, 2 * np.pi, n, endpoint=False)
     pos = np.stack([4 * np.cos(ang), 4 * np.sin(ang)], 1)
     sc = one_env(pos, np.zeros((n, 2)), -pos, 0.3, 1.4, segs=[(-0.5, -0.5, 0.5, 0.5)])
-    worst, mism, fb = teacher_forced(sc, 80)
+    worst, mism, fb = teacher_forced(sc, 80, flags=cw.CROWD_FLAG_FORCE_TILED if tiled else 0)
     assert fb > 0
     assert mism == 0
     assert worst <= VEL_TOL, worst
@@ -206,6 +210,22 @@ def test_lattice_exact_ties(tiled, K):
     sc = one_env(pos, np.zeros_like(pos), goal, 0.3, 1.2, R=3.0, K=K)
     worst, mism, fb = teacher_forced(sc, 2, flags=cw.CROWD_FLAG_FORCE_TILED if tiled else 0)
     assert mism == 0 and worst <= VEL_TOL
+
+
+@pytest.mark.parametrize("tiled", [False, True])
+def test_overlapping_crowd(tiled):
+    """200 agents of radius 0.3 m dropped into a 2 x 2 m square (nearly every
+    pair overlaps): every candidate of the block is within R, K = 32 lists,
+    colliding half-planes and fallbacks for most agents."""
+    from paper_2505_00690_gb300 import crowd as cw
+
+    rng = np.random.default_rng(5)
+    pos = rng.uniform(0, 2, (200, 2))
+    goal = rng.uniform(-10, 12, (200, 2))
+    sc = one_env(pos, np.zeros_like(pos), goal, 0.3, 1.4, R=5.0, K=32)
+    worst, mism, fb = teacher_forced(sc, 5, flags=cw.CROWD_FLAG_FORCE_TILED if tiled else 0)
+    assert fb > 0
+    assert mism == 0 and worst <= VEL_TOL, worst
 
 
 def test_robot_agent_follows_command():
