@@ -80,10 +80,16 @@ __device__ __forceinline__ float2 advance_goal(const GoalQueue& gq, int g, int e
     return gq.queue[(size_t)g * gq.q + (gq.cyclic ? (k + 1) % gq.q : k + 1)];
 }
 
-// Per-thread work tallies (only reported when counting is on).
+// Per-thread work tallies (only reported when counting is on).  32-bit: ten
+// 64-bit counters live through the whole update held 20 registers and made
+// the persistent tiled update spill more (16 x 20,000 crowd 2.7 % slower).
+// A thread's counts cover one step: a tiled launch is one step, and the
+// shared-memory kernel flushes them after every step when counting, so a
+// count would need over 4e9 items of one kind in one step of one thread
+// (tens of millions of agents at one point) to wrap.
 struct Tally {
-    unsigned long long agent_steps = 0, candidates = 0, agent_lines = 0, obstacle_lines = 0, segment_tests = 0,
-                       lp_checks = 0, lp_solves = 0, lp_solve_lines = 0, fallbacks = 0, pairs_in_range = 0;
+    unsigned agent_steps = 0, candidates = 0, agent_lines = 0, obstacle_lines = 0, segment_tests = 0,
+             lp_checks = 0, lp_solves = 0, lp_solve_lines = 0, fallbacks = 0, pairs_in_range = 0;
 };
 
 template <int KMAX>
@@ -352,7 +358,7 @@ __device__ __forceinline__ void select_neighbors(const Src& src, const CellGeom&
             consider(o, cu);
         }
     }
-    w.candidates += ncand;
+    w.candidates += (unsigned)ncand;
     const int cnt = top.cnt;
     // tie[s]: keys s and s + 1 are near-equal (s + 1 < cnt)
     bool any_tie = false;

@@ -217,7 +217,7 @@ __device__ __forceinline__ void group_select(const Grp<G>& g, const Src& src, in
     top.init();
     for (int yy = ya; yy <= yb; ++yy) {
         const int2 r = src.row(yy, xa, xb);
-        if (g.lane == 0) w.candidates += (unsigned long long)(r.y - r.x);
+        if (g.lane == 0) w.candidates += (unsigned)(r.y - r.x);
         for (int u = r.x + g.lane; u < r.y; u += G) {
             const float4 o = src.cand(u);
             const float dx = o.x - me.x, dy = o.y - me.y;

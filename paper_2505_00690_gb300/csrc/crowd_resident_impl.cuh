@@ -572,6 +572,10 @@ __global__ void __launch_bounds__(kMaxThreads, G >= 4 ? 2 : 1) resident_kernel(R
             float4* tmp = S.pv;
             S.pv = S.nv;
             S.nv = tmp;
+            if (a.work) {  // the 32-bit tallies cover one step
+                flush_tally(tally, a.work);
+                tally = Tally{};
+            }
         }
         __syncthreads();
         for (int i = threadIdx.x; i < c.n; i += blockDim.x) a.state[c.base + i] = S.pv[i];
