@@ -178,8 +178,8 @@ constexpr int kQueueThreads = 128;
 constexpr int kQueueItem = 32;
 // CTAs of the persistent update per SM the compiler budgets registers for
 // (65,536 / (6 x 128) = 85, 80 a thread): on the 500-step 16 x 20,000 crowd
-// 6 CTAs (24 warps per SM) ran 263.9 ms, 5 CTAs (96 registers) 268.8 ms,
-// 4 (128 registers) slower still, 7 and 8 (more spills) 276.5 ms
+// 6 CTAs (24 warps per SM) ran 257.1 ms, 5 CTAs (96 registers) 265.9 ms,
+// 7 (72 registers, more spills) 266.4 ms; 4 (128 registers) was slower than 5
 #ifndef CROWD_QUEUE_MINB
 #define CROWD_QUEUE_MINB 6
 #endif
