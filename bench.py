@@ -209,9 +209,18 @@ def side_workload(name, sc, steps, tune_steps, plain_envs, stream, flush, reps=3
     cr.close()
     best = min(ms)
     value = sc.n_agents * steps / (best / 1e3)
+    # the same rollout once more (untimed) with the work counted, so that
+    # workloads of different density compare by work rate as well
+    counted = cw.Crowd(sc, flags=cw.CROWD_FLAG_COUNT_WORK, stream=stream.cuda_stream)
+    counted.step(rv, n_steps=steps)
+    work = counted.work()
+    counted.close()
+    flops = algorithmic_flops(work)
     plain = plain_form(sc, min(steps, 20), plain_envs, stream)
     return {"workload": name, "envs": sc.n_envs, "agents": sc.n_agents, "rollout_steps": steps,
             "value": value, "unit": UNIT, "ms_per_rollout": best, "ms_all": ms, "tuning": tuning,
+            "counted_flop_per_agent_step": flops / max(1, work["agent_steps"]),
+            "counted_tflops": flops / (best / 1e3) / 1e12,
             "plain": plain, "batched_over_plain": value / plain["value"]}
 
 

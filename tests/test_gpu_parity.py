@@ -284,6 +284,29 @@ def test_env_alone_equals_env_in_batch():
     full.close()
 
 
+def test_env_alone_equals_env_in_full_uneven_batch():
+    """The full uneven batch (1024 environments of 16-512 agents, Sec. 3.3):
+    an environment stepped alone gives the same bits as inside the batch, on
+    both paths (the batch's launch shape, queue order and, on the tiled path,
+    cell size and work items differ from the lone environment's)."""
+    from paper_2505_00690_gb300 import crowd as cw
+
+    sc = scenes.uneven_batch(0, steps=12)
+    es = sc.env_start
+    sizes = np.diff(es)
+    pick = [int(np.argmin(sizes)), int(np.argmax(sizes)), 3, 511, 1023]
+    for flags in (0, cw.CROWD_FLAG_FORCE_TILED):
+        full = _crowd(sc, flags)
+        full.step(n_steps=12)
+        F = full.state()
+        full.close()
+        for e in pick:
+            one = _crowd(sc.subset([e]), flags)
+            one.step(n_steps=12)
+            assert np.array_equal(one.state(), F[es[e]:es[e + 1]]), (flags, e, sizes[e])
+            one.close()
+
+
 @pytest.mark.parametrize("tiled", [False, True])
 def test_checkpoint_resume_equals_continuous_run(tiled):
     """Checkpoint/resume: the state read after 15 steps, loaded into a new
