@@ -673,18 +673,23 @@ def test_deferred_fallback_modes_teacher_forced(coop):
     assert worst <= VEL_TOL, worst
 
 
-def test_agent_order_and_deferred_fallback_change_no_bit():
+@pytest.mark.parametrize("which", ["urban", "uneven"])
+def test_agent_order_and_deferred_fallback_change_no_bit(which):
     """In-place and deferred one-lane fallbacks run the same arithmetic on the
     same lines, and the agent order only changes which thread computes an
     agent: every combination gives the same bits."""
-    sc = scenes.urban_block(2, n_envs=8, steps=40)
+    if which == "urban":
+        sc = scenes.urban_block(2, n_envs=8, steps=40)
+    else:
+        sc = scenes.uneven_batch(4, n_envs=12, n_lo=16, n_hi=600, steps=40)
+    rv = sc.robot_vel[:40] if sc.robot_vel is not None else None
     ref = None
     for block, coop, order, split in ((0, 0, 0, 1), (0, 2, 0, 1), (0, 0, 1, 1), (0, 2, 1, 2), (256, 2, 1, 1),
-                                      (64, 0, 1, 2), (512, 2, 0, 1)):
+                                      (64, 0, 1, 2), (512, 2, 0, 1), (128, 0, 1, 3)):
         cr = _crowd(sc, 0)
         cr.set_tuning(block_threads=block, coop_fallback=coop, cell_split=split, agent_order=order)
         assert cr.tuning()["agent_order"] == order
-        cr.step(sc.robot_vel[:40], n_steps=40)
+        cr.step(rv, n_steps=40)
         out = cr.state()
         cr.close()
         if ref is None:
