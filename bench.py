@@ -47,9 +47,9 @@ WORKLOAD = ("dense_crowd: 16 envs x 20,000 pedestrians (2 per m^2 in 100x100 m, 
 ROLLOUT = 500
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch of the update
 # kernel on this workload (ncu, one pass, `bench.py --profile-case dense`:
-# the second step of the rollout, 31,893,504 + 67,853,056 bytes), or None
-# when the kernel has changed since the counters were taken
-UPDATE_DRAM_BYTES = 99_746_560
+# the second step of the rollout), or None when the kernel has changed since
+# the counters were taken
+UPDATE_DRAM_BYTES = None
 FP32_LANES_PER_SM = 128
 N_SMS = 152
 SERVE_RATES = (200.0, 400.0, 800.0, 1600.0)

@@ -180,7 +180,10 @@ struct GlobalAgents {
     __device__ __forceinline__ float4 params(int j) const { return __ldg(&par[j]); }
 };
 
-template <int KMAX, class Src>
+// INSTR: compiled with the statistics and work-count code (false: a launch
+// with neither, whose work tallies are then dead code, so that the plain
+// step holds no registers for them).
+template <int KMAX, class Src, bool INSTR = true>
 __device__ __forceinline__ void tile_agent(const TiledStepArgs& a, const AgentParams& ap, const TiledEnv& te,
                                            const Src& src, int slot, Tally& w, unsigned long long& ca,
                                            unsigned long long& cs, double& speed) {
@@ -191,7 +194,7 @@ __device__ __forceinline__ void tile_agent(const TiledStepArgs& a, const AgentPa
     const int k = cell_of(te, me.x, me.y);
     const int cx = k % te.W, cy = k / te.W;
 
-    if (a.mode != kTiledStep) {
+    if (INSTR && a.mode != kTiledStep) {
         // collision events of the input state (the previous step's result)
         const int xa = max(cx - 1, 0), xb = min(cx + 1, te.W - 1);
         for (int yy = max(cy - 1, 0); yy <= min(cy + 1, te.H - 1); ++yy) {
@@ -217,7 +220,7 @@ __device__ __forceinline__ void tile_agent(const TiledStepArgs& a, const AgentPa
 
     NbList<KMAX> nb;
     select_neighbors<KMAX, true>(src, CellGeom{te.x0, te.y0, te.inv_c}, cx, cy, te.W, te.H, i, me, ap.R, ap.K, nb, w,
-                           te.span, a.work != nullptr);
+                           te.span, INSTR && a.work != nullptr);
     if (a.nbr_out) {
         int* out = a.nbr_out + (size_t)g * ap.K;
 #pragma unroll
@@ -242,7 +245,7 @@ __device__ __forceinline__ void tile_agent(const TiledStepArgs& a, const AgentPa
     nx.z = v.x;
     nx.w = v.y;
     a.state_out[g] = nx;
-    if (a.stats && i != te.robot && pr.w == 0.f) {
+    if (INSTR && a.stats && i != te.robot && pr.w == 0.f) {
         speed += (double)sqrtf(v.x * v.x + v.y * v.y);
         const float2 gl = __ldg(&a.goal[g]);
         const float gx = gl.x - nx.x, gy = gl.y - nx.y;
@@ -365,7 +368,7 @@ __device__ __forceinline__ double warp_sum(double v) {
 // held its whole CTA until its slowest warp was done, and environments of
 // any size share the launch.  The per-agent work is tile_agent's, so the
 // results are those of tiled_update bit for bit.
-template <int KMAX>
+template <int KMAX, bool INSTR>
 __global__ void __launch_bounds__(kQueueThreads, kQueueMinBlocks) tiled_update_queue(TiledStepArgs a) {
     const int lane = threadIdx.x & 31;
     const AgentParams ap{a.R, a.dt, a.tau, a.tau_o, a.robot_alpha, a.K, a.segs, a.err, a.seg_vd};
@@ -387,9 +390,9 @@ __global__ void __launch_bounds__(kQueueThreads, kQueueMinBlocks) tiled_update_q
         double speed = 0.0;
         if (q < te.n) {
             const GlobalSource src{a.sorted_pv, a.sorted_id, a.start + te.co, te.W};
-            tile_agent<KMAX>(a, ap, te, src, te.base + q, w, ca, cs, speed);
+            tile_agent<KMAX, GlobalSource, INSTR>(a, ap, te, src, te.base + q, w, ca, cs, speed);
         }
-        if (a.stats) {
+        if (INSTR && a.stats) {
             ca = warp_sum(ca);
             cs = warp_sum(cs);
             speed = warp_sum(speed);
@@ -401,7 +404,7 @@ __global__ void __launch_bounds__(kQueueThreads, kQueueMinBlocks) tiled_update_q
             }
         }
     }
-    if (a.work) flush_tally(w, a.work);
+    if (INSTR && a.work) flush_tally(w, a.work);
 }
 
 constexpr int kVehicleThreads = 256;
@@ -468,7 +471,10 @@ cudaError_t update_k(const TiledStepArgs& a, int max_tiles, cudaStream_t s) {
     if (a.use_queue) {
         const int warps = kQueueThreads / 32;
         const int grid = std::max(1, std::min(a.queue_grid, (a.n_items + warps - 1) / warps));
-        tiled_update_queue<KMAX><<<grid, kQueueThreads, 0, s>>>(a);
+        if (a.work || a.stats || a.mode != kTiledStep)
+            tiled_update_queue<KMAX, true><<<grid, kQueueThreads, 0, s>>>(a);
+        else
+            tiled_update_queue<KMAX, false><<<grid, kQueueThreads, 0, s>>>(a);
     } else {
         tiled_update<KMAX><<<dim3(max_tiles, a.n_envs), kUpdateThreads, tiled_smem_bytes(a.halo_cap), s>>>(a);
     }
@@ -478,7 +484,7 @@ cudaError_t update_k(const TiledStepArgs& a, int max_tiles, cudaStream_t s) {
 template <int KMAX>
 int queue_blocks() {
     int n = 0;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, tiled_update_queue<KMAX>, kQueueThreads, 0) ==
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, tiled_update_queue<KMAX, true>, kQueueThreads, 0) ==
                    cudaSuccess
                ? n
                : 0;
