@@ -149,6 +149,7 @@ struct crowd_ctx {
     int n_items = 0;
     int* tqueue = nullptr;      // work-item counter of the persistent update
     int queue_grid = 0;         // its CTAs: as many as fit on the GPU
+    int queue_grid_plain = 0;   // the same for its form without statistics and work counts
     cudaGraphExec_t graph = nullptr;
     int64_t graph_kernels = 0;    // kernel launches one replay of `graph` performs
     int64_t kernel_launches = 0;  // kernels this handle's steps enqueued (graph replays by their kernels)
@@ -618,6 +619,7 @@ TiledStepArgs tiled_args(crowd_t h, float dt, const float2* rv, int s, int n_ste
     a.n_items = h->n_items;
     a.queue = h->tqueue;
     a.queue_grid = h->queue_grid;
+    a.queue_grid_plain = h->queue_grid_plain;
     a.R = h->p.neighbor_dist;
     a.dt = dt;
     a.tau = h->p.time_horizon;
@@ -1000,12 +1002,14 @@ crowd_status crowd_create(int32_t n_envs, const int32_t* agents_per_env, const f
     }
     h->sms = sms;
     if (h->n_tiled) {
-        const int per_sm = tiled_queue_blocks_per_sm(p->max_neighbors);
-        if (per_sm < 1) {
+        const int per_sm = tiled_queue_blocks_per_sm(p->max_neighbors, false);
+        const int per_sm_plain = tiled_queue_blocks_per_sm(p->max_neighbors, true);
+        if (per_sm < 1 || per_sm_plain < 1) {
             cuda_fail(cudaGetLastError(), "occupancy of the persistent tiled update");
             return bail(CROWD_ECUDA);
         }
         h->queue_grid = per_sm * sms;
+        h->queue_grid_plain = per_sm_plain * sms;
     }
     apply_tuning(h, h->tune);
 

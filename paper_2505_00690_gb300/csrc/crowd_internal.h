@@ -176,14 +176,21 @@ constexpr int kTiledUpdateThreads = 256;
 // agents per work item (one warp).
 constexpr int kQueueThreads = 128;
 constexpr int kQueueItem = 32;
-// CTAs of the persistent update per SM the compiler budgets registers for
-// (65,536 / (6 x 128) = 85, 80 a thread): on the 500-step 16 x 20,000 crowd
-// 6 CTAs (24 warps per SM) ran 257.1 ms, 5 CTAs (96 registers) 265.9 ms,
-// 7 (72 registers, more spills) 266.4 ms; 4 (128 registers) was slower than 5
+// CTAs of the persistent update per SM the compiler budgets registers for.
+// With the statistics and work-count code (65,536 / (6 x 128) = 85, 80 a
+// thread): on the 500-step 16 x 20,000 crowd 6 CTAs (24 warps per SM) ran
+// 257.1 ms, 5 CTAs (96 registers) 265.9 ms, 7 (72 registers, more spills)
+// 266.4 ms; 4 (128 registers) was slower than 5.  The plain form (neither,
+// so fewer live values) at 7 CTAs (72 registers, 28 warps) ran 242.4 ms
+// against 247.9 ms at 6.
 #ifndef CROWD_QUEUE_MINB
 #define CROWD_QUEUE_MINB 6
 #endif
+#ifndef CROWD_QUEUE_PLAIN_MINB
+#define CROWD_QUEUE_PLAIN_MINB 7
+#endif
 constexpr int kQueueMinBlocks = CROWD_QUEUE_MINB;
+constexpr int kQueuePlainMinBlocks = CROWD_QUEUE_PLAIN_MINB;
 // Cells of R / 2 are used when the tiled agents of a handle number at least
 // this many rounds of kTiledUpdateThreads on every SM.
 constexpr int kFineCellRounds = 4;
@@ -237,12 +244,13 @@ struct TiledStepArgs {
     // persistent update (use_queue != 0): work items of 32 consecutive sorted
     // slots of one environment, item_start[t] the first item of tiled
     // environment t ([n_envs + 1]), taken from the counter *queue (zeroed by
-    // tiled_scan) by the warps of queue_grid CTAs
+    // tiled_scan) by the warps of queue_grid CTAs (queue_grid_plain for the
+    // form without statistics and work counts)
     int use_queue;
     const int* item_start;
     int n_items;
     int* queue;
-    int queue_grid;
+    int queue_grid, queue_grid_plain;
     float R, dt, tau, tau_o, robot_alpha;
     int K;
     int seg_vd;               // 1: velocity-dependent segment half-planes
@@ -261,7 +269,7 @@ constexpr int kHaloCap = 3072;
 size_t tiled_smem_bytes(int halo_cap);
 // CTAs of the persistent tiled update kernel for neighbour cap K that fit on
 // one SM (0 on error).
-int tiled_queue_blocks_per_sm(int K);
+int tiled_queue_blocks_per_sm(int K, bool plain);
 // One-time kernel attributes of the tiled path (before any capture).
 cudaError_t tiled_init(int halo_cap);
 // Enqueue one thread setting the device step counter.

@@ -369,7 +369,8 @@ __device__ __forceinline__ double warp_sum(double v) {
 // any size share the launch.  The per-agent work is tile_agent's, so the
 // results are those of tiled_update bit for bit.
 template <int KMAX, bool INSTR>
-__global__ void __launch_bounds__(kQueueThreads, kQueueMinBlocks) tiled_update_queue(TiledStepArgs a) {
+__global__ void __launch_bounds__(kQueueThreads, INSTR ? kQueueMinBlocks : kQueuePlainMinBlocks)
+    tiled_update_queue(TiledStepArgs a) {
     const int lane = threadIdx.x & 31;
     const AgentParams ap{a.R, a.dt, a.tau, a.tau_o, a.robot_alpha, a.K, a.segs, a.err, a.seg_vd};
     Tally w;
@@ -470,11 +471,12 @@ template <int KMAX>
 cudaError_t update_k(const TiledStepArgs& a, int max_tiles, cudaStream_t s) {
     if (a.use_queue) {
         const int warps = kQueueThreads / 32;
-        const int grid = std::max(1, std::min(a.queue_grid, (a.n_items + warps - 1) / warps));
+        const int need = (a.n_items + warps - 1) / warps;
         if (a.work || a.stats || a.mode != kTiledStep)
-            tiled_update_queue<KMAX, true><<<grid, kQueueThreads, 0, s>>>(a);
+            tiled_update_queue<KMAX, true><<<std::max(1, std::min(a.queue_grid, need)), kQueueThreads, 0, s>>>(a);
         else
-            tiled_update_queue<KMAX, false><<<grid, kQueueThreads, 0, s>>>(a);
+            tiled_update_queue<KMAX, false><<<std::max(1, std::min(a.queue_grid_plain, need)), kQueueThreads, 0, s>>>(
+                a);
     } else {
         tiled_update<KMAX><<<dim3(max_tiles, a.n_envs), kUpdateThreads, tiled_smem_bytes(a.halo_cap), s>>>(a);
     }
@@ -482,12 +484,12 @@ cudaError_t update_k(const TiledStepArgs& a, int max_tiles, cudaStream_t s) {
 }
 
 template <int KMAX>
-int queue_blocks() {
+int queue_blocks(bool plain) {
     int n = 0;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, tiled_update_queue<KMAX, true>, kQueueThreads, 0) ==
-                   cudaSuccess
-               ? n
-               : 0;
+    const cudaError_t e =
+        plain ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, tiled_update_queue<KMAX, false>, kQueueThreads, 0)
+              : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, tiled_update_queue<KMAX, true>, kQueueThreads, 0);
+    return e == cudaSuccess ? n : 0;
 }
 
 }  // namespace
@@ -501,12 +503,12 @@ cudaError_t launch_set_step(long long* p, long long value, cudaStream_t s) {
 
 size_t tiled_smem_bytes(int halo_cap) { return (size_t)halo_cap * (sizeof(float4) + sizeof(int)); }
 
-int tiled_queue_blocks_per_sm(int K) {
+int tiled_queue_blocks_per_sm(int K, bool plain) {
     switch (resident_kmax(K)) {
-        case 8: return queue_blocks<8>();
-        case 10: return queue_blocks<10>();
-        case 16: return queue_blocks<16>();
-        default: return queue_blocks<32>();
+        case 8: return queue_blocks<8>(plain);
+        case 10: return queue_blocks<10>(plain);
+        case 16: return queue_blocks<16>(plain);
+        default: return queue_blocks<32>(plain);
     }
 }
 
