@@ -181,13 +181,15 @@ constexpr int kQueueItem = 32;
 // thread): on the 500-step 16 x 20,000 crowd 6 CTAs (24 warps per SM) ran
 // 257.1 ms, 5 CTAs (96 registers) 265.9 ms, 7 (72 registers, more spills)
 // 266.4 ms; 4 (128 registers) was slower than 5.  The plain form (neither,
-// so fewer live values) at 7 CTAs (72 registers, 28 warps) ran 242.4 ms
-// against 247.9 ms at 6.
+// so fewer live values) at 8 CTAs (64 registers, 32 warps) ran 238.4 ms,
+// against 247.9 ms at 6, 242.1 ms at 7, 245.6 ms at 9 (56 registers) and
+// 262.6 ms at 10 (48 registers): below 64 registers the spills cost more
+// than the added warps hide.
 #ifndef CROWD_QUEUE_MINB
 #define CROWD_QUEUE_MINB 6
 #endif
 #ifndef CROWD_QUEUE_PLAIN_MINB
-#define CROWD_QUEUE_PLAIN_MINB 7
+#define CROWD_QUEUE_PLAIN_MINB 8
 #endif
 constexpr int kQueueMinBlocks = CROWD_QUEUE_MINB;
 constexpr int kQueuePlainMinBlocks = CROWD_QUEUE_PLAIN_MINB;
