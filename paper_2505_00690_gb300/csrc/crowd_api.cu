@@ -148,6 +148,9 @@ struct crowd_ctx {
     int* item_start = nullptr;  // [n_tiled + 1] work items (32 sorted slots) of the persistent update
     int n_items = 0;
     int* tqueue = nullptr;      // work-item counter of the persistent update
+    int* item_order = nullptr;  // [n_items] dispatch order of the items (ItemSched)
+    unsigned char* item_bucket = nullptr;  // [n_items] cost class of each item in the last step
+    ItemSched* sched = nullptr;
     int queue_grid = 0;         // its CTAs: as many as fit on the GPU
     int queue_grid_plain = 0;   // the same for its form without statistics and work counts
     cudaGraphExec_t graph = nullptr;
@@ -171,7 +174,7 @@ struct crowd_ctx {
                         lane_cum, veh_pref, ep_steps, ep_state, ep_goal, ep_gidx, ep_veh, ep_mask, pool_start, pool,
                         segs, robot_vel, nbr, reach, stats, work, tenvs, state_b, sorted_pv, key, rank,
                         count, start, sorted_id, seg_cell_start, seg_cell_ids, seg_grid, d_step, item_start,
-                        tqueue};
+                        tqueue, item_order, item_bucket, sched};
         for (void* q : ptrs)
             if (q) cudaFree(q);
     }
@@ -618,6 +621,9 @@ TiledStepArgs tiled_args(crowd_t h, float dt, const float2* rv, int s, int n_ste
     a.item_start = h->item_start;
     a.n_items = h->n_items;
     a.queue = h->tqueue;
+    a.item_order = a.use_queue ? h->item_order : nullptr;
+    a.item_bucket = a.use_queue ? h->item_bucket : nullptr;
+    a.sched = a.use_queue ? h->sched : nullptr;
     a.queue_grid = h->queue_grid;
     a.queue_grid_plain = h->queue_grid_plain;
     a.R = h->p.neighbor_dist;
@@ -921,6 +927,9 @@ crowd_status crowd_create(int32_t n_envs, const int32_t* agents_per_env, const f
         ALLOC(d_step, 1);
         ALLOC(item_start, item_start.size());
         ALLOC(tqueue, 1);
+        ALLOC(item_order, std::max(h->n_items, 1));
+        ALLOC(item_bucket, std::max(h->n_items, 1));
+        ALLOC(sched, 1);
     }
     ALLOC(env_start, n_envs + 1);
     ALLOC(seg_start, n_envs + 1);
@@ -968,6 +977,14 @@ crowd_status crowd_create(int32_t n_envs, const int32_t* agents_per_env, const f
         (e = cudaMemsetAsync(h->reach, 0xff, sizeof(int) * std::max<int64_t>(N, 1), h->stream)) != cudaSuccess ||
         (e = cudaMemsetAsync(h->stats, 0, sizeof(EnvStats) * std::max(n_envs, 1), h->stream)) != cudaSuccess) {
         cuda_fail(e, "initialise buffers");
+        return bail(CROWD_ECUDA);
+    }
+    ItemSched sched0{};
+    sched0.count[0] = h->n_items;  // no costs yet: every item in the first class
+    if (h->sched && ((e = cudaMemsetAsync(h->item_bucket, 0, std::max(h->n_items, 1), h->stream)) != cudaSuccess ||
+                     (e = cudaMemcpyAsync(h->sched, &sched0, sizeof(ItemSched), cudaMemcpyHostToDevice, h->stream)) !=
+                         cudaSuccess)) {
+        cuda_fail(e, "initialise the item order");
         return bail(CROWD_ECUDA);
     }
     if (h->count && (e = cudaMemsetAsync(h->count, 0, sizeof(int) * total_cells, h->stream)) != cudaSuccess) {

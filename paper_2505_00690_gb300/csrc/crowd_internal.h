@@ -154,6 +154,22 @@ struct Tuning {
 };
 
 // One large environment of the tiled path (static uniform grid, cell >= R).
+// Order in which the persistent tiled update hands out its work items:
+// longest first, so that the step does not end waiting for a costly item
+// taken last.  Each item's cost (clock cycles of its warp) in one step puts
+// it in one of kItemBuckets classes relative to the previous step's mean
+// cost (>= 2, 1.4, 1, 0.7 times the mean, and below); the next step hands
+// out the classes in that order.  The order changes no result: every agent
+// is computed the same way whichever warp takes it and when.
+constexpr int kItemBuckets = 5;
+struct ItemSched {
+    unsigned long long cost_sum;  // cycles of the items of the step in progress
+    float mean;                   // mean item cost of the last finished step (0: none yet)
+    int count_next[kItemBuckets]; // items per class in the step in progress
+    int count[kItemBuckets];      // items per class of the last finished step (the order being handed out)
+    int cursor[kItemBuckets];     // placement cursors of the order being built
+};
+
 struct TiledEnv {
     int e;          // environment id
     int base, n;    // agents [base, base + n)
@@ -253,6 +269,11 @@ struct TiledStepArgs {
     int n_items;
     int* queue;
     int queue_grid, queue_grid_plain;
+    // dispatch order of the items (longest first, by the cost each item took
+    // in the previous step; see ItemSched), or null for item order
+    int* item_order;
+    unsigned char* item_bucket;  // [n_items] cost class of each item in the previous step
+    ItemSched* sched;
     float R, dt, tau, tau_o, robot_alpha;
     int K;
     int seg_vd;               // 1: velocity-dependent segment half-planes

@@ -128,6 +128,25 @@ __global__ void __launch_bounds__(kScanThreads) tiled_scan(TiledStepArgs a) {
         __syncthreads();
     }
     if (threadIdx.x == 0) a.start[te.co + C] = carry;
+    if (a.item_order) {
+        // this environment's work items into the dispatch order, by the cost
+        // class each took in the previous step (classes in order, the items
+        // of a class in any order)
+        __shared__ int s_off[kItemBuckets];
+        if (threadIdx.x == 0) {
+            int o = 0;
+            for (int b = 0; b < kItemBuckets; ++b) {
+                s_off[b] = o;
+                o += a.sched->count[b];
+            }
+        }
+        __syncthreads();
+        const int i1 = a.item_start[blockIdx.x + 1];
+        for (int i = a.item_start[blockIdx.x] + threadIdx.x; i < i1; i += blockDim.x) {
+            const int b = a.item_bucket[i];
+            a.item_order[s_off[b] + atomicAdd(&a.sched->cursor[b], 1)] = i;
+        }
+    }
 }
 
 __global__ void __launch_bounds__(kCountThreads) tiled_scatter(TiledStepArgs a) {
@@ -373,12 +392,17 @@ __global__ void __launch_bounds__(kQueueThreads, INSTR ? kQueueMinBlocks : kQueu
     tiled_update_queue(TiledStepArgs a) {
     const int lane = threadIdx.x & 31;
     const AgentParams ap{a.R, a.dt, a.tau, a.tau_o, a.robot_alpha, a.K, a.segs, a.err, a.seg_vd};
+    __shared__ long long s_t0[kQueueThreads / 32];  // start clock of each warp's item
     Tally w;
     for (;;) {
         int item = 0;
         if (lane == 0) item = atomicAdd(a.queue, 1);
         item = __shfl_sync(0xffffffffu, item, 0);
         if (item >= a.n_items) break;
+        if (a.item_order) {
+            item = a.item_order[item];
+            if (lane == 0) s_t0[threadIdx.x >> 5] = clock64();  // kept in shared memory, not a register
+        }
         int lo = 0, hi = a.n_envs - 1;  // environment of the item
         while (lo < hi) {
             const int mid = (lo + hi + 1) >> 1;
@@ -392,6 +416,18 @@ __global__ void __launch_bounds__(kQueueThreads, INSTR ? kQueueMinBlocks : kQueu
         if (q < te.n) {
             const GlobalSource src{a.sorted_pv, a.sorted_id, a.start + te.co, te.W};
             tile_agent<KMAX, GlobalSource, INSTR>(a, ap, te, src, te.base + q, w, ca, cs, speed);
+        }
+        if (a.item_order) {
+            // the item's cost class for the next step's dispatch order
+            __syncwarp();
+            if (lane == 0) {
+                const long long c = clock64() - s_t0[threadIdx.x >> 5];
+                const float m = a.sched->mean, cf = (float)c;
+                const int b = cf >= 2.f * m ? 0 : cf >= 1.4f * m ? 1 : cf >= m ? 2 : cf >= 0.7f * m ? 3 : 4;
+                a.item_bucket[item] = (unsigned char)b;
+                atomicAdd(&a.sched->count_next[b], 1);
+                atomicAdd(&a.sched->cost_sum, (unsigned long long)(c > 0 ? c : 0));
+            }
         }
         if (INSTR && a.stats) {
             ca = warp_sum(ca);
@@ -465,6 +501,22 @@ __global__ void tiled_finish_step(TiledStepArgs a) {
     if (a.stats && a.mode != kTiledStatsOnly)
         for (int k = 0; k < a.n_envs; ++k) a.stats[a.envs[k].e].steps += 1;
     if (a.mode != kTiledStatsOnly) *a.step_index += 1;
+    if (a.sched) {
+        // the classes of this step's items become the next step's order; the
+        // counts move only when the update classed every item
+        ItemSched& q = *a.sched;
+        int n = 0;
+        for (int b = 0; b < kItemBuckets; ++b) n += q.count_next[b];
+        if (n == a.n_items) {
+            q.mean = a.n_items > 0 ? (float)((double)q.cost_sum / (double)a.n_items) : 0.f;
+            for (int b = 0; b < kItemBuckets; ++b) q.count[b] = q.count_next[b];
+        }
+        for (int b = 0; b < kItemBuckets; ++b) {
+            q.count_next[b] = 0;
+            q.cursor[b] = 0;
+        }
+        q.cost_sum = 0;
+    }
 }
 
 template <int KMAX>
