@@ -49,7 +49,7 @@ ROLLOUT = 500
 # kernel on this workload (ncu, one pass, `bench.py --profile-case dense`:
 # the second step of the rollout), or None when the kernel has changed since
 # the counters were taken
-UPDATE_DRAM_BYTES = None
+UPDATE_DRAM_BYTES = 146_685_184
 FP32_LANES_PER_SM = 128
 N_SMS = 152
 SERVE_RATES = (200.0, 400.0, 800.0, 1600.0)
